@@ -1,0 +1,363 @@
+"""Plain FP64 CPU oracle of the Fast Finite Shearlet Transform (FFST).
+
+TEST INFRASTRUCTURE ONLY.  This module is the correctness reference for the
+CUDA library: only the test suite, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import it.  The product path never does, and
+it shares no code, tables or constants with the CUDA sources.
+
+Everything here is the paper's definition written out directly, in float64,
+with NumPy's FFT as the only library step (Haeuser & Steidl, "Fast Finite
+Shearlet Transform: a tutorial", arXiv:1202.1773):
+
+* windows ``v``, ``b``, ``psi1_hat``, ``psi2_hat``, ``varphi``, ``phi_hat``:
+  Sec. 2.1 eqs. (v), (b), (Psi1), (Psi2) and Sec. 2.4 eq. (phi);
+* cones C^h, C^v, C^x: Sec. 2.3;
+* discretisation j0, a_j, s_{j,k}, the index set Omega: Sec. 3.1;
+* frequency grid Xi (X = 2^{2 j0 - 1}): Sec. 3.5.1;
+* plane index i <-> (kappa, j, k), eta = 2^{j0+2} - 3: Sec. 3.5.2;
+* forward transform: Sec. 3.1 eq. (shearletTransform);
+* inverse transform: Sec. 3.3 eq. (inverseShearletTransform);
+* real-coefficient mirroring of the Nyquist row/column: Sec. 3.8.1.
+
+Readings of passages where the paper is silent or ambiguous (each is listed
+in the project's design notes):
+
+* axis: omega_1 runs along columns (x), omega_2 along rows (y); the
+  coefficient stack is stored as ``[eta, M, N]`` (plane-major);
+* grid: each axis spans [-X, X] with its own spacing, xi = omega * X /
+  floor(L/2) (the paper's odd-size symmetric linspace, padded by one sample
+  for even sizes and the last sample dropped, written as a product);
+* cone membership is decided exactly on the integer frequency indices;
+* the Nyquist fix replaces psi(w1, -M/2) by sqrt((psi(w1)^2 + psi(-w1)^2)/2)
+  (same for the column -N/2), which reproduces the paper's mirroring example
+  and keeps sum_i psi_i^2 = 1.
+
+Pins: every function here is checked in ``tests/test_oracle_*.py`` against
+closed forms, the paper's lemmas/theorems, printed tables and worked
+examples, brute-force DFTs and invariants.  No function is "parity unpinned"
+except ``spectrum`` for non-square sizes, where the paper does not fix the
+grid (see the reading above); square sizes are pinned by transpose symmetry.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Sec. 2.1: auxiliary functions
+# ---------------------------------------------------------------------------
+
+
+def v(x):
+    """Meyer auxiliary function, Sec. 2.1 eq. (v).
+
+    0 for x < 0, 35x^4 - 84x^5 + 70x^6 - 20x^7 on [0, 1], 1 for x > 1.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    # the same polynomial in nested (Horner) form, which rounds less near x = 1
+    poly = x**4 * (35.0 + x * (-84.0 + x * (70.0 - 20.0 * x)))
+    return np.where(x < 0.0, 0.0, np.where(x > 1.0, 1.0, poly))
+
+
+def b(omega):
+    """Bump b(omega), Sec. 2.1 eq. (b): supported on 1 <= |omega| <= 4."""
+    w = np.abs(np.asarray(omega, dtype=np.float64))
+    rise = np.sin(0.5 * np.pi * v(w - 1.0))
+    fall = np.cos(0.5 * np.pi * v(0.5 * w - 1.0))
+    return np.where((w >= 1.0) & (w <= 2.0), rise,
+                    np.where((w > 2.0) & (w <= 4.0), fall, 0.0))
+
+
+def psi1_hat(omega):
+    """Radial (scale) window, Sec. 2.1 eq. (Psi1): sqrt(b(2w)^2 + b(w)^2)."""
+    return np.sqrt(b(2.0 * np.asarray(omega, dtype=np.float64)) ** 2 + b(omega) ** 2)
+
+
+def psi2_hat(omega):
+    """Directional window, Sec. 2.1 eq. (Psi2).
+
+    sqrt(v(1 + w)) for w <= 0 and sqrt(v(1 - w)) for w > 0.
+    """
+    w = np.asarray(omega, dtype=np.float64)
+    return np.where(w <= 0.0, np.sqrt(v(1.0 + w)), np.sqrt(v(1.0 - w)))
+
+
+def varphi(omega):
+    """1-D scaling window of Sec. 2.4 (the function written varphi there)."""
+    w = np.abs(np.asarray(omega, dtype=np.float64))
+    mid = np.cos(0.5 * np.pi * v(2.0 * w - 1.0))
+    return np.where(w <= 0.5, 1.0, np.where(w < 1.0, mid, 0.0))
+
+
+def phi_hat(xi1, xi2):
+    """Cone-adapted scaling function, Sec. 2.4 eq. (phi).
+
+    varphi(xi1) where |xi2| <= |xi1|, varphi(xi2) where |xi1| < |xi2|.
+    """
+    xi1 = np.asarray(xi1, dtype=np.float64)
+    xi2 = np.asarray(xi2, dtype=np.float64)
+    return np.where(np.abs(xi2) <= np.abs(xi1), varphi(xi1), varphi(xi2))
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.1 / 3.5: discretisation, grid and indexing
+# ---------------------------------------------------------------------------
+
+
+def default_scales(rows: int, cols: int) -> int:
+    """j0 = floor(1/2 log2 max(M, N)), Sec. 3.1 (table in Sec. 3.5.1).
+
+    Integer arithmetic: floor(log2 n) is n.bit_length() - 1.
+    """
+    n = max(int(rows), int(cols))
+    if n < 1:
+        raise ValueError("empty image")
+    return (n.bit_length() - 1) // 2
+
+
+def num_planes(scales: int) -> int:
+    """eta = 1 + sum_{j<j0} 2^{j+2} = 2^{j0+2} - 3, Sec. 3.5.2."""
+    return 1 + sum(2 ** (j + 2) for j in range(scales))
+
+
+def plane_table(scales: int):
+    """Index i -> (kappa, j, k), Sec. 3.5.2.
+
+    kappa is one of 'lowpass', 'h', 'v', 'seam'.  Plane 0 is the low-pass;
+    then per scale j (J = 2^j), rotating counter-clockwise: h with k = 0,
+    h with k = -1 .. -(J-1), the seam shearlet with k = -J, v with
+    k = -(J-1) .. J-1, the seam shearlet with k = +J, and h with
+    k = J-1 .. 1 (the paper's "k = 2^j, ..., 1" starts at the seam already
+    listed, so the h run starts at J-1).
+    """
+    table = [("lowpass", -1, 0)]
+    for j in range(scales):
+        J = 2**j
+        table.append(("h", j, 0))
+        for k in range(-1, -J, -1):
+            table.append(("h", j, k))
+        table.append(("seam", j, -J))
+        for k in range(-J + 1, J):
+            table.append(("v", j, k))
+        table.append(("seam", j, J))
+        for k in range(J - 1, 0, -1):
+            table.append(("h", j, k))
+    assert len(table) == num_planes(scales)
+    return table
+
+
+def freq_index(L: int) -> np.ndarray:
+    """Integer frequencies of Omega (Sec. 3.1) in FFT storage order.
+
+    Omega covers -floor(L/2) .. ceil(L/2)-1; storage position p holds
+    p for p < ceil(L/2) and p - L otherwise (numpy.fft order).
+    """
+    p = np.arange(L, dtype=np.int64)
+    half = (L + 1) // 2
+    return np.where(p < half, p, p - L)
+
+
+def grid_spacing(L: int, scales: int) -> float:
+    """Grid step of one axis of Xi, Sec. 3.5.1: X / floor(L/2), X = 2^{2 j0 - 1}.
+
+    For odd L the paper's grid is linspace(-X, X, L), step 2X/(L-1) =
+    X/floor(L/2); for even L it pads to L+1 and drops the last sample,
+    which keeps the same step.
+    """
+    X = 2.0 ** (2 * scales - 1)
+    h = L // 2
+    if h == 0:
+        return 0.0
+    return X / h
+
+
+def grid(rows: int, cols: int, scales: int):
+    """Integer indices (o1, o2) and grid points (xi1, xi2), shape (M, N).
+
+    xi1 (omega_1) varies along columns, xi2 (omega_2) along rows.
+    """
+    o1 = freq_index(cols)[None, :] * np.ones((rows, 1), dtype=np.int64)
+    o2 = freq_index(rows)[:, None] * np.ones((1, cols), dtype=np.int64)
+    xi1 = o1 * grid_spacing(cols, scales)
+    xi2 = o2 * grid_spacing(rows, scales)
+    return o1, o2, xi1, xi2
+
+
+def cones(rows: int, cols: int, o1, o2):
+    """Masks of C^h, C^v and the seam lines C^x on the grid, Sec. 2.3.
+
+    |xi2| < |xi1|  <=>  |o2| * floor(N/2) < |o1| * floor(M/2), decided in
+    integers.  The origin belongs to none of them.
+    """
+    lhs = np.abs(o2) * (cols // 2)
+    rhs = np.abs(o1) * (rows // 2)
+    nonzero = (o1 != 0) | (o2 != 0)
+    ch = (lhs < rhs) & nonzero
+    cv = (lhs > rhs) & nonzero
+    cx = (lhs == rhs) & nonzero
+    return ch, cv, cx
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.1 / 3.4.1 / 3.8.1: spectra
+# ---------------------------------------------------------------------------
+
+
+def _ratio(num, den, mask):
+    out = np.zeros(num.shape, dtype=np.float64)
+    np.divide(num, den, out=out, where=mask)
+    return out
+
+
+def spectrum_raw(rows: int, cols: int, scales: int, i: int) -> np.ndarray:
+    """Spectrum of plane i on Xi without the Nyquist fix, FFT storage order.
+
+    Sec. 3.1 eq. (shearletTransform):
+      low-pass:  phi_hat(xi)                                      (Sec. 2.4)
+      h, |k|<J:  psi1(4^-j xi1) psi2(2^j xi2/xi1 + k) on C^h      (eq. horizontalShearlet)
+      v, |k|<J:  psi1(4^-j xi2) psi2(2^j xi1/xi2 + k) on C^v      (eq. verticalShearlet)
+      seam |k|=J: the glued sum psi^h + psi^v + psi^x: the h formula on
+                  C^h and on the seam lines, the v formula on C^v.
+    """
+    kappa, j, k = plane_table(scales)[i]
+    o1, o2, xi1, xi2 = grid(rows, cols, scales)
+    if kappa == "lowpass":
+        return phi_hat(xi1, xi2)
+    ch, cv, cx = cones(rows, cols, o1, o2)
+    a = 4.0 ** (-j)
+    J = 2.0**j
+    h_part = psi1_hat(a * xi1) * psi2_hat(J * _ratio(xi2, xi1, xi1 != 0) + k)
+    v_part = psi1_hat(a * xi2) * psi2_hat(J * _ratio(xi1, xi2, xi2 != 0) + k)
+    if kappa == "h":
+        return np.where(ch, h_part, 0.0)
+    if kappa == "v":
+        return np.where(cv, v_part, 0.0)
+    return np.where(ch | cx, h_part, 0.0) + np.where(cv, v_part, 0.0)
+
+
+def nyquist_mirror(psi: np.ndarray) -> np.ndarray:
+    """Real-coefficient fix of Sec. 3.8.1 on one spectrum (FFT order).
+
+    For even M the row omega_2 = -M/2 has no conjugate partner inside the
+    grid; its values are mirrored around the omega_1 = 0 axis and scaled by
+    1/sqrt(2):  psi'(w1) = sqrt((psi(w1)^2 + psi(-w1)^2) / 2).  The same is
+    done for the column omega_1 = -N/2 when N is even.  Where psi(w1) and
+    psi(-w1) have disjoint supports this is the paper's mirrored-and-scaled
+    row; where they are equal (axis shearlets) it leaves the row unchanged.
+    """
+    out = psi.copy()
+    M, N = psi.shape
+    if M % 2 == 0:
+        r = M // 2
+        row = psi[r, :]
+        mirror = row[(-np.arange(N)) % N]
+        out[r, :] = np.sqrt(0.5 * (row**2 + mirror**2))
+    if N % 2 == 0:
+        c = N // 2
+        col = psi[:, c]
+        mirror = col[(-np.arange(M)) % M]
+        out[:, c] = np.sqrt(0.5 * (col**2 + mirror**2))
+    return out
+
+
+def spectrum(rows: int, cols: int, scales: int, i: int, real_fix: bool = True) -> np.ndarray:
+    """Spectrum psi_hat_i of plane i (FFT storage order), fix applied by default.
+
+    The fix is on by default, as the paper's ``realReal`` option (Sec. 3.5.3).
+    """
+    raw = spectrum_raw(rows, cols, scales, i)
+    return nyquist_mirror(raw) if real_fix else raw
+
+
+def spectra(rows: int, cols: int, scales: int | None = None, real_fix: bool = True) -> np.ndarray:
+    """Stack of all eta spectra, shape (eta, M, N), Sec. 3.5.2."""
+    if scales is None:
+        scales = default_scales(rows, cols)
+    return np.stack([spectrum(rows, cols, scales, i, real_fix)
+                     for i in range(num_planes(scales))])
+
+
+def frame_sum(rows: int, cols: int, scales: int | None = None, real_fix: bool = True) -> np.ndarray:
+    """sum_i psi_hat_i^2 on the grid (Sec. 3.6, frame tightness)."""
+    if scales is None:
+        scales = default_scales(rows, cols)
+    acc = np.zeros((rows, cols))
+    for i in range(num_planes(scales)):
+        acc += spectrum(rows, cols, scales, i, real_fix) ** 2
+    return acc
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.1 / 3.3: transforms
+# ---------------------------------------------------------------------------
+
+
+def forward_complex(f: np.ndarray, scales: int | None = None, real_fix: bool = True) -> np.ndarray:
+    """c_i = ifft2(psi_hat_i * fft2(f)) as complex numbers, Sec. 3.1 eq. (shearletTransform)."""
+    f = np.asarray(f, dtype=np.float64)
+    M, N = f.shape
+    if scales is None:
+        scales = default_scales(M, N)
+    F = np.fft.fft2(f)
+    return np.stack([np.fft.ifft2(spectrum(M, N, scales, i, real_fix) * F)
+                     for i in range(num_planes(scales))])
+
+
+def forward_plane(F: np.ndarray, scales: int, i: int) -> np.ndarray:
+    """One real coefficient plane from a precomputed F = fft2(f)."""
+    M, N = F.shape
+    return np.real(np.fft.ifft2(spectrum(M, N, scales, i) * F))
+
+
+def forward(f: np.ndarray, scales: int | None = None) -> np.ndarray:
+    """Real coefficient stack (eta, M, N): the real part of ``forward_complex``.
+
+    With the Nyquist fix the imaginary part is rounding noise (Sec. 3.8.1).
+    """
+    f = np.asarray(f, dtype=np.float64)
+    M, N = f.shape
+    if scales is None:
+        scales = default_scales(M, N)
+    F = np.fft.fft2(f)
+    return np.stack([forward_plane(F, scales, i) for i in range(num_planes(scales))])
+
+
+def adjoint(c: np.ndarray, scales: int | None = None) -> np.ndarray:
+    """T* c = Re ifft2( sum_i psi_hat_i * fft2(c_i) ), Sec. 3.3.
+
+    For a Parseval frame T* = T^-1 (Sec. 3.2, eq. shearlet_transform_as_matrix).
+    """
+    c = np.asarray(c, dtype=np.float64)
+    _, M, N = c.shape
+    if scales is None:
+        scales = default_scales(M, N)
+    acc = np.zeros((M, N), dtype=np.complex128)
+    for i in range(num_planes(scales)):
+        acc += spectrum(M, N, scales, i) * np.fft.fft2(c[i])
+    return np.real(np.fft.ifft2(acc))
+
+
+def inverse(c: np.ndarray, scales: int | None = None) -> np.ndarray:
+    """Re ifft2( sum_i psi_hat_i * fft2(c_i) / sum_i psi_hat_i^2 ), Sec. 3.3.
+
+    Sec. 3.3 eq. (inverseShearletTransform) sums the products; the division
+    by sum_i psi_hat_i^2 (identically 1 for the Parseval frame of Sec. 3.2,
+    up to rounding) is kept as an explicit normalisation.
+    """
+    c = np.asarray(c, dtype=np.float64)
+    _, M, N = c.shape
+    if scales is None:
+        scales = default_scales(M, N)
+    acc = np.zeros((M, N), dtype=np.complex128)
+    den = np.zeros((M, N))
+    for i in range(num_planes(scales)):
+        s = spectrum(M, N, scales, i)
+        acc += s * np.fft.fft2(c[i])
+        den += s * s
+    return np.real(np.fft.ifft2(acc / den))
+
+
+def mean_abs(c: np.ndarray) -> np.ndarray:
+    """d(i) = 1/(MN) sum |c(., ., i)|, Sec. 3.5.2 eq. (shearlet_meanvalue)."""
+    c = np.asarray(c)
+    return np.abs(c).reshape(c.shape[0], -1).mean(axis=1)
