@@ -1,0 +1,363 @@
+"""Benchmark: FFST forward + inverse throughput (shearlet coefficients / s).
+
+Workload (one step): forward transform of one 2048x2048 float32 image with
+j0 = 5 scales (eta = 125 planes, 524,288,000 coefficients, stack stored as
+float32), then the inverse transform of that stack back to an image.  Inputs
+are seeded synthetic cartoon images (ellipses + polygons + N(0, 0.1^2)),
+already resident in device memory; the 2.1 GB coefficient stack written and
+read every step is far larger than L2, so no explicit flush is needed.
+
+Prints one JSON line.  `value` = eta*M*N*steps*ranks / (max over ranks of
+the timed region); `e2e` = the same metric through the public API with the
+image copied host->device and the reconstruction copied back every step;
+`roofline` = the dominant kernel's algorithmic HBM bytes per launch over its
+CUDA-event duration, against the measured copy bandwidth; `cpu_baseline`
+= the FP64 oracle timed on this host's cores on a bounded sample.
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on the same workload definition, one bounded sample per step.
+Multi-GPU (torchrun): every rank runs its own images (independent replicas,
+weak scaling, no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+ROWS, COLS, SCALES = 2048, 2048, 5
+METRIC = "fwd+inv shearlet coeffs/s (2048x2048 f32, J=5, eta=125)"
+UNIT = "coeffs/s"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks / throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _init_pg(world, backend):
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def _max_over_ranks(x: float, world: int, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+
+ORACLE_STEP_PLANES = 1      # --impl reference: planes per timed step (~5 s of CPU)
+ORACLE_BASELINE_PLANES = 3  # cpu_baseline of the GPU arm (~15 s of CPU)
+
+
+def oracle_sample_seconds(f64, planes):
+    """Time the FP64 oracle on a bounded sample of one step: fft2 of the image,
+    `planes` forward planes, the inverse contributions of those planes and the
+    final ifft2.  Returns (seconds, coefficients processed)."""
+    from oracle import ffst_oracle as o
+
+    M, N = f64.shape
+    t0 = time.perf_counter()
+    F = np.fft.fft2(f64)
+    acc = np.zeros((M, N), dtype=np.complex128)
+    den = np.zeros((M, N))
+    for i in range(planes):
+        c = o.forward_plane(F, SCALES, i)
+        s = o.spectrum(M, N, SCALES, i)
+        acc += s * np.fft.fft2(c)
+        den += s * s
+    np.real(np.fft.ifft2(acc / np.where(den > 0, den, 1.0)))
+    return time.perf_counter() - t0, planes * M * N
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if world > 1 and rank != 0:
+        return 0
+    from paper_1202_1773_gb300 import inputs
+
+    f = inputs.scaled_cartoon(ROWS, COLS, seed=5).astype(np.float64)
+    for _ in range(args.warmup):
+        oracle_sample_seconds(f, planes=1)
+    tot_s, tot_c = 0.0, 0
+    for _ in range(args.steps):
+        s, c = oracle_sample_seconds(f, ORACLE_STEP_PLANES)
+        tot_s += s
+        tot_c += c
+    value = tot_c / tot_s
+    sample = (f"per step: fft2 + {ORACLE_STEP_PLANES} of 125 planes forward and inverse + ifft2 of the "
+              f"2048x2048 J=5 workload (FP64 NumPy oracle), rate scaled to coefficients/s")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "FFST fwd+inv, 2048x2048 f32 image, J=5, eta=125", "rows": ROWS, "cols": COLS,
+                       "scales": SCALES},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+
+    import paper_1202_1773_gb300 as ffst
+    from paper_1202_1773_gb300 import build, inputs
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _init_pg(world, "nccl")
+    build.build()
+
+    plan = ffst.Plan(ROWS, COLS, SCALES, device=dev)
+    eta = plan.num_planes
+    coeffs_per_step = eta * ROWS * COLS
+    pool = [torch.from_numpy(inputs.scaled_cartoon(ROWS, COLS, seed=100 + 8 * rank + q)).to(dev) for q in range(4)]
+    stack = torch.empty(plan.shape, dtype=torch.float32, device=dev)
+    rec = torch.empty((ROWS, COLS), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(q):
+        plan.forward(pool[q % len(pool)], out=stack)
+        plan.inverse(stack, out=rec)
+
+    for q in range(args.warmup):
+        step(q)
+    torch.cuda.synchronize(dev)
+
+    # timed region: per-kernel timers on (events on the launch stream)
+    plan.timing_reset()
+    plan.timing(True)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.5)
+    _barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for q in range(args.steps):
+        step(q)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    _barrier(world)
+    clocks = sampler.stop() if sampler else None
+    plan.timing(False)
+    ms = t0.elapsed_time(t1)
+    ms_max = _max_over_ranks(ms, world, dev)
+    kernels = plan.timing_read()
+    value = coeffs_per_step * args.steps * world / (ms_max / 1e3)
+
+    # forward / inverse split (untimed loop, events only)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd_ms = inv_ms = 0.0
+    for q in range(max(3, args.steps // 2)):
+        e[0].record(stream)
+        plan.forward(pool[q % len(pool)], out=stack)
+        e[1].record(stream)
+        plan.inverse(stack, out=rec)
+        e[2].record(stream)
+        torch.cuda.synchronize(dev)
+        fwd_ms += e[0].elapsed_time(e[1])
+        inv_ms += e[1].elapsed_time(e[2])
+    nsplit = max(3, args.steps // 2)
+
+    # end to end through the public API with host buffers
+    host_img = [torch.from_numpy(inputs.scaled_cartoon(ROWS, COLS, seed=200 + q)).pin_memory() for q in range(2)]
+    host_out = torch.empty((ROWS, COLS), dtype=torch.float32).pin_memory()
+    dimg = torch.empty((ROWS, COLS), dtype=torch.float32, device=dev)
+
+    def e2e_step(q):
+        dimg.copy_(host_img[q % 2], non_blocking=True)
+        plan.forward(dimg, out=stack)
+        plan.inverse(stack, out=rec)
+        host_out.copy_(rec, non_blocking=True)
+
+    for q in range(2):
+        e2e_step(q)
+    torch.cuda.synchronize(dev)
+    _barrier(world)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for q in range(args.steps):
+        e2e_step(q)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = _max_over_ranks(a.elapsed_time(b), world, dev)
+    e2e_value = coeffs_per_step * args.steps * world / (e2e_ms / 1e3)
+
+    if rank != 0:
+        return 0
+
+    # roofline of the dominant kernel (largest total time in the timed region)
+    peak, peak_kind = _peaks()
+    name, (kms, kn, kbytes) = max(kernels.items(), key=lambda kv: kv[1][0])
+    step_bytes = 2.0 * coeffs_per_step * 4 + 8.0 * ROWS * COLS
+    if kbytes > 0 and kn > 0:
+        achieved = (kbytes / kn) / ((kms / kn) / 1e3) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "launches": kn, "avg_ms": kms / kn}
+    else:
+        roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,
+                "traffic": None, "launches": kn, "avg_ms": kms / max(kn, 1),
+                "note": "intermediates stay in L2: no algorithmic HBM bytes"}
+    step_gbs = step_bytes * args.steps / (ms_max / 1e3) / 1e9
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        f64 = pool[0].double().cpu().numpy()
+        oracle_sample_seconds(f64, planes=1)
+        s, c = oracle_sample_seconds(f64, ORACLE_BASELINE_PLANES)
+        cpu = {"value": c / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"fft2 + {ORACLE_BASELINE_PLANES} of 125 planes fwd+inv + ifft2, FP64 NumPy, 2048x2048 J=5"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "FFST fwd+inv, 2048x2048 f32 image, J=5, eta=125, f32 stack",
+                   "rows": ROWS, "cols": COLS, "scales": SCALES, "planes": eta,
+                   "coeffs_per_step": coeffs_per_step,
+                   "l2": "inputs larger than L2 (2.10 GB coefficient stack written and read per step)",
+                   "parallelism": f"replicas x{world}"},
+        "fwd_ms": fwd_ms / nsplit, "inv_ms": inv_ms / nsplit,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * ROWS * COLS,
+                "d2h_bytes_per_step": 4 * ROWS * COLS},
+        "roofline": roof,
+        "roofline_step": {"bound": "hbm", "achieved": step_gbs, "peak": peak, "unit": "GB/s",
+                          "frac": step_gbs / peak, "bytes_per_step": step_bytes, "peak_source": peak_kind},
+        "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                        "alg_bytes_per_step": v[2] / args.steps} for k, v in kernels.items() if v[1]},
+        "gpu_launches": int(sum(v[1] for v in kernels.values())),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

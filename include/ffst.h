@@ -1,0 +1,157 @@
+/*
+ * ffst.h - C ABI of the GB300-native Fast Finite Shearlet Transform (FFST).
+ *
+ * The transform follows Haeuser & Steidl, "Fast Finite Shearlet Transform:
+ * a tutorial" (arXiv:1202.1773):
+ *   forward  c_i = ifft2( psi_hat_i * fft2(f) ),  i = 0..eta-1     (Sec. 3.1, eq. shearletTransform)
+ *   inverse  f   = ifft2( sum_i psi_hat_i * fft2(c_i) / sum_i psi_hat_i^2 )  (Sec. 3.3, eq. inverseShearletTransform)
+ *   adjoint  f   = ifft2( sum_i psi_hat_i * fft2(c_i) )                      (Sec. 3.2, U^T of eq. shearlet_transform_as_matrix)
+ * with the cone-adapted Meyer shearlets of Sec. 2 on the grid of Sec. 3.5.1,
+ * the plane order of Sec. 3.5.2 and the real-coefficient mirroring of
+ * Sec. 3.8.1 (always on).  All arithmetic is FP32 on the device; FP64 is
+ * used only on the host, once per plan, for twiddle and window tables.
+ *
+ * Conventions shared by every entry point:
+ *  - Images are row-major rows x cols float32 (M x N).  Row index m1 goes
+ *    with omega_2, column index m2 with omega_1 (Sec. 3.5.2: "the first both
+ *    components refer to the omega_2 and omega_1 coordinates").
+ *  - A coefficient or spectra stack is plane-major [eta][rows][cols]: plane i
+ *    is one contiguous row-major M x N image, planes in the order of Sec. 3.5.2.
+ *  - All pointers named "device" must be device memory of the current CUDA
+ *    device, allocated and owned by the caller.  The plan owns its own
+ *    workspace and tables and frees them in ffst_destroy.
+ *  - Calls that take a stream are asynchronous and stream-ordered: they only
+ *    enqueue kernels on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream); no host<->device copies and no synchronisation.  Two calls on
+ *    the same plan must not run concurrently (they share the workspace).
+ *  - Errors are returned as ffst_status codes; nothing is thrown across the
+ *    ABI.  ffst_last_error() returns a thread-local message for the last
+ *    failing call on the calling thread.  Argument errors are detected on the
+ *    host before anything is enqueued; FFST_ERR_CUDA reports a failed CUDA
+ *    runtime call (launch or allocation), after which the outputs are
+ *    unspecified.
+ *  - Supported sizes: rows and cols are powers of two with 8 <= rows, cols
+ *    <= 4096; scales in 1..8 (or <= 0 for the default j0 of Sec. 3.1).
+ *    Other sizes return FFST_ERR_UNSUPPORTED_SIZE.
+ */
+#ifndef FFST_H
+#define FFST_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ffst_plan_s* ffst_plan_t;
+
+typedef enum {
+  FFST_OK = 0,
+  FFST_ERR_INVALID_ARG = 1,      /* null pointer, bad index, bad storage code   */
+  FFST_ERR_UNSUPPORTED_SIZE = 2, /* rows/cols/scales outside the supported set  */
+  FFST_ERR_OUT_OF_MEMORY = 3,    /* device or host allocation failed            */
+  FFST_ERR_CUDA = 4,             /* a CUDA runtime call failed                  */
+  FFST_ERR_TIMEOUT = 5           /* a bounded device-side wait ran out          */
+} ffst_status;
+
+/* Storage type of a coefficient stack.  Arithmetic is FP32 in every case. */
+typedef enum {
+  FFST_STORE_F32 = 0,  /* float32 coefficients, plane_scale unused (may be NULL) */
+  FFST_STORE_F16 = 1,  /* IEEE half: stores c_i * s_i, s_i a power of two       */
+  FFST_STORE_BF16 = 2  /* bfloat16: stores c_i * s_i                             */
+} ffst_storage;
+
+/* Plane kinds returned by ffst_plane_index (kappa of Sec. 3.1). */
+enum { FFST_CONE_LOWPASS = 0, FFST_CONE_H = 1, FFST_CONE_V = 2, FFST_CONE_SEAM = 3 };
+
+/*
+ * Build a plan for rows x cols images with `scales` scales (j0 of Sec. 3.1;
+ * <= 0 selects j0 = floor(1/2 log2 max(rows, cols))).  The number of planes
+ * is eta = 2^(j0+2) - 3 (Sec. 3.5.2).  Generates the FP64 window/twiddle
+ * tables on the host, uploads them, computes every plane's spectral support
+ * on the device (synchronously, on an internal stream) and allocates the
+ * workspace.  Uses the current CUDA device.  On success *out owns all of it.
+ */
+ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* out);
+
+/* Query a plan.  Any output pointer may be NULL. */
+ffst_status ffst_plan_info(ffst_plan_t plan, int* rows, int* cols, int* scales, int* num_planes);
+
+/*
+ * Plane index i -> (kappa, j, k) of Sec. 3.5.2 (the analogue of the paper's
+ * shearletScaleShear helper).  cone is one of FFST_CONE_*; for the low-pass
+ * j = -1 and k = 0.  Returns FFST_ERR_INVALID_ARG for i outside [0, eta).
+ */
+ffst_status ffst_plane_index(ffst_plan_t plan, int i, int* cone, int* j, int* k);
+
+/*
+ * Write every spectrum psi_hat_i (real, with the Sec. 3.8.1 fix) on the full
+ * M x N frequency grid in FFT storage order (index p <-> omega = p for
+ * p < ceil(L/2), p - L otherwise) into `psi` (device, [eta][rows][cols]
+ * float32).  For tests and inspection; the transforms never read spectra
+ * from memory, they generate them in registers.
+ */
+ffst_status ffst_spectra(ffst_plan_t plan, float* psi, void* stream);
+
+/*
+ * Forward transform, Sec. 3.1 eq. (shearletTransform).
+ *   img:         device, rows x cols float32, read only.
+ *   coeffs:      device, [eta][rows][cols] of the storage type (float, __half
+ *                or __nv_bfloat16), fully overwritten.
+ *   storage:     an ffst_storage code.
+ *   plane_scale: device float[eta]; required (non-NULL) for F16/BF16, where the
+ *                forward writes s_i (a power of two chosen from a bound on
+ *                max|c_i|) and stores c_i * s_i; ignored for F32.
+ */
+ffst_status ffst_forward(ffst_plan_t plan, const float* img, void* coeffs, int storage,
+                         float* plane_scale, void* stream);
+
+/*
+ * Inverse transform, Sec. 3.3 eq. (inverseShearletTransform), normalised by
+ * sum_i psi_hat_i^2 (which the Parseval frame of Sec. 3.2 makes 1).
+ *   coeffs:      device [eta][rows][cols] of the storage type, read only.
+ *   plane_scale: device float[eta] written by ffst_forward (F16/BF16 only);
+ *                stored values are multiplied by 1/s_i on load.
+ *   img:         device rows x cols float32, overwritten.
+ */
+ffst_status ffst_inverse(ffst_plan_t plan, const void* coeffs, int storage,
+                         const float* plane_scale, float* img, void* stream);
+
+/*
+ * Adjoint T* c = ifft2( sum_i psi_hat_i * fft2(c_i) ) (Sec. 3.2: for a
+ * Parseval frame the adjoint U^T is the inverse).  Same arguments as
+ * ffst_inverse; omits the normalisation, so it is the exact adjoint of the
+ * FP32 forward and the backward pass of the differentiable transform.
+ */
+ffst_status ffst_adjoint(ffst_plan_t plan, const void* coeffs, int storage,
+                         const float* plane_scale, float* img, void* stream);
+
+/* Free a plan and everything it owns (synchronises the device first).  NULL is a no-op. */
+void ffst_destroy(ffst_plan_t plan);
+
+/* Thread-local message describing the last failing call on this thread ("" if none). */
+const char* ffst_last_error(void);
+
+/* Static name of a status code. */
+const char* ffst_status_string(int status);
+
+/*
+ * Per-kernel timing: while enabled, every kernel the plan launches is
+ * bracketed by CUDA events on its launch stream and its duration is added
+ * to a per-kind total.  ffst_timing_read synchronises on those events and
+ * reports, for kernel kind `kind` (0 .. ffst_timing_kinds()-1), its name,
+ * total milliseconds, launch count and the algorithmic HBM bytes of those
+ * launches (the bytes a fused kernel must move: see the project's design
+ * notes).  ffst_timing_reset clears the totals.
+ */
+ffst_status ffst_timing_enable(ffst_plan_t plan, int enable);
+ffst_status ffst_timing_reset(ffst_plan_t plan);
+int ffst_timing_kinds(void);
+ffst_status ffst_timing_read(ffst_plan_t plan, int kind, const char** name, double* total_ms,
+                             long long* launches, double* algorithmic_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFST_H */

@@ -1,0 +1,229 @@
+"""GB300-native Fast Finite Shearlet Transform (arXiv:1202.1773).
+
+The transform runs in libffst.so, a C-ABI CUDA library for sm_103a
+(``include/ffst.h``).  This package is its binding:
+
+* ``ffst_plan``, ``ffst_spectra``, ``ffst_forward``, ``ffst_inverse``,
+  ``ffst_adjoint``, ... : the C entry points, argument marshalling only
+  (device pointers as ints or tensors, stream handles);
+* ``Plan``: the same calls on torch CUDA tensors (PyTorch provides device
+  memory and the current stream, nothing else);
+* ``FFSTFunction`` / ``shearlet_transform``: the forward transform as a
+  differentiable layer whose backward pass is the hand-written adjoint.
+
+There is no CPU fallback: without the built library every call raises.
+"""
+
+from __future__ import annotations
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    FFST_ERR_CUDA,
+    FFST_ERR_INVALID_ARG,
+    FFST_ERR_OUT_OF_MEMORY,
+    FFST_ERR_TIMEOUT,
+    FFST_ERR_UNSUPPORTED_SIZE,
+    FFST_OK,
+    FFST_STORE_BF16,
+    FFST_STORE_F16,
+    FFST_STORE_F32,
+    FFSTError,
+    ffst_adjoint,
+    ffst_destroy,
+    ffst_forward,
+    ffst_inverse,
+    ffst_plan,
+    ffst_plan_info,
+    ffst_plane_index,
+    ffst_spectra,
+    ffst_timing_enable,
+    ffst_timing_kinds,
+    ffst_timing_read,
+    ffst_timing_reset,
+)
+
+__all__ = ["Plan", "FFSTFunction", "shearlet_transform", "FFSTError"] + [n for n, _, _ in _lib.SIGNATURES]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _storage_of(dtype) -> int:
+    torch = _torch()
+    if dtype == torch.float32:
+        return FFST_STORE_F32
+    if dtype == torch.float16:
+        return FFST_STORE_F16
+    if dtype == torch.bfloat16:
+        return FFST_STORE_BF16
+    raise ValueError(f"unsupported coefficient dtype {dtype}")
+
+
+class Plan:
+    """A libffst plan for rows x cols float32 images on one CUDA device."""
+
+    def __init__(self, rows: int, cols: int, scales: int = 0, device=None):
+        torch = _torch()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.handle = ffst_plan(rows, cols, scales)
+        self.rows, self.cols, self.scales, self.num_planes = ffst_plan_info(self.handle)
+
+    # -- bookkeeping ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "handle", None):
+            ffst_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def plane_index(self, i: int):
+        """(kind, j, k) of plane i in the order of Sec. 3.5.2."""
+        cone, j, k = ffst_plane_index(self.handle, i)
+        return _lib.CONE_NAMES[cone], j, k
+
+    def plane_table(self):
+        return [self.plane_index(i) for i in range(self.num_planes)]
+
+    @property
+    def shape(self):
+        return (self.num_planes, self.rows, self.cols)
+
+    def _stream(self):
+        return _torch().cuda.current_stream(self.device).cuda_stream
+
+    def _check_img(self, img):
+        torch = _torch()
+        if img.device != self.device or img.dtype != torch.float32 or tuple(img.shape) != (self.rows, self.cols):
+            raise ValueError(f"expected a {self.rows}x{self.cols} float32 tensor on {self.device}, "
+                             f"got {tuple(img.shape)} {img.dtype} on {img.device}")
+        if not img.is_contiguous():
+            raise ValueError("image must be contiguous")
+
+    def _check_coeffs(self, c):
+        if c.device != self.device or tuple(c.shape) != self.shape or not c.is_contiguous():
+            raise ValueError(f"expected a contiguous {self.shape} tensor on {self.device}, "
+                             f"got {tuple(c.shape)} on {c.device}")
+
+    # -- transforms -----------------------------------------------------------
+    def spectra(self, out=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        self._check_coeffs(out)
+        ffst_spectra(self.handle, out, self._stream())
+        return out
+
+    def forward(self, img, dtype=None, out=None, plane_scale=None):
+        """Coefficient stack [eta, rows, cols].  For float16/bfloat16 storage
+        also returns the per-plane scales (stored values are c_i * s_i)."""
+        torch = _torch()
+        self._check_img(img)
+        if out is None:
+            out = torch.empty(self.shape, dtype=dtype or torch.float32, device=self.device)
+        self._check_coeffs(out)
+        storage = _storage_of(out.dtype)
+        if storage != FFST_STORE_F32 and plane_scale is None:
+            plane_scale = torch.empty(self.num_planes, dtype=torch.float32, device=self.device)
+        ffst_forward(self.handle, img, out, storage, plane_scale if storage != FFST_STORE_F32 else None,
+                     self._stream())
+        return (out, plane_scale) if storage != FFST_STORE_F32 else out
+
+    def _synth(self, fn, coeffs, plane_scale, out):
+        torch = _torch()
+        self._check_coeffs(coeffs)
+        storage = _storage_of(coeffs.dtype)
+        if storage != FFST_STORE_F32 and plane_scale is None:
+            raise ValueError("plane_scale is required for float16/bfloat16 coefficients")
+        if out is None:
+            out = torch.empty((self.rows, self.cols), dtype=torch.float32, device=self.device)
+        self._check_img(out)
+        fn(self.handle, coeffs, storage, plane_scale if storage != FFST_STORE_F32 else None, out, self._stream())
+        return out
+
+    def inverse(self, coeffs, plane_scale=None, out=None):
+        return self._synth(ffst_inverse, coeffs, plane_scale, out)
+
+    def adjoint(self, coeffs, plane_scale=None, out=None):
+        return self._synth(ffst_adjoint, coeffs, plane_scale, out)
+
+    # -- timing ---------------------------------------------------------------
+    def timing(self, enable: bool):
+        ffst_timing_enable(self.handle, enable)
+
+    def timing_reset(self):
+        ffst_timing_reset(self.handle)
+
+    def timing_read(self):
+        """{kernel kind: (total_ms, launches, algorithmic_bytes)}"""
+        out = {}
+        for k in range(ffst_timing_kinds()):
+            name, ms, n, by = ffst_timing_read(self.handle, k)
+            out[name] = (ms, n, by)
+        return out
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class _Adjoint(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, coeffs, plan):
+            ctx.plan = plan
+            return plan.adjoint(coeffs.contiguous())
+
+        @staticmethod
+        def backward(ctx, grad_img):
+            return _Forward.apply(grad_img.contiguous(), ctx.plan), None
+
+    class _Forward(torch.autograd.Function):
+        """x -> T x (Sec. 3.1); backward g -> T* g (the hand-written adjoint)."""
+
+        @staticmethod
+        def forward(ctx, img, plan):
+            ctx.plan = plan
+            return plan.forward(img.contiguous())
+
+        @staticmethod
+        def backward(ctx, grad_coeffs):
+            return _Adjoint.apply(grad_coeffs.contiguous(), ctx.plan), None
+
+    return _Forward, _Adjoint
+
+
+_AUTOGRAD = None
+
+
+def _autograd():
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _make_autograd()
+    return _AUTOGRAD
+
+
+class _FFSTFunctionProxy:
+    """``FFSTFunction.apply(img, plan)``: the differentiable forward transform."""
+
+    @staticmethod
+    def apply(img, plan):
+        return _autograd()[0].apply(img, plan)
+
+
+FFSTFunction = _FFSTFunctionProxy
+
+
+def shearlet_transform(img, plan: Plan):
+    """Differentiable T img; gradients flow through ``ffst_adjoint``."""
+    return _autograd()[0].apply(img, plan)
+
+
+def shearlet_adjoint(coeffs, plan: Plan):
+    """Differentiable T* coeffs; its gradient is the forward transform."""
+    return _autograd()[1].apply(coeffs, plan)

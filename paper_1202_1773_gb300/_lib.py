@@ -1,0 +1,165 @@
+"""ctypes binding of libffst.so: the C ABI declared in include/ffst.h.
+
+Each ``ffst_*`` function here has the name and argument order of the C
+entry point and does argument marshalling only (integers, device pointers
+as Python ints, stream handles).  A missing or unloadable library raises:
+there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+FFST_OK = 0
+FFST_ERR_INVALID_ARG = 1
+FFST_ERR_UNSUPPORTED_SIZE = 2
+FFST_ERR_OUT_OF_MEMORY = 3
+FFST_ERR_CUDA = 4
+FFST_ERR_TIMEOUT = 5
+
+FFST_STORE_F32 = 0
+FFST_STORE_F16 = 1
+FFST_STORE_BF16 = 2
+
+CONE_NAMES = {0: "lowpass", 1: "h", 2: "v", 3: "seam"}
+
+# (name, restype, argtypes) of every entry point in include/ffst.h
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+SIGNATURES = [
+    ("ffst_plan", _I, [_I, _I, _I, ctypes.POINTER(_VP)]),
+    ("ffst_plan_info", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    ("ffst_plane_index", _I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    ("ffst_spectra", _I, [_VP, _VP, _VP]),
+    ("ffst_forward", _I, [_VP, _VP, _VP, _I, _VP, _VP]),
+    ("ffst_inverse", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
+    ("ffst_adjoint", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
+    ("ffst_destroy", None, [_VP]),
+    ("ffst_last_error", ctypes.c_char_p, []),
+    ("ffst_status_string", ctypes.c_char_p, [_I]),
+    ("ffst_timing_enable", _I, [_VP, _I]),
+    ("ffst_timing_reset", _I, [_VP]),
+    ("ffst_timing_kinds", _I, []),
+    ("ffst_timing_read", _I, [_VP, _I, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+]
+
+_LIB = None
+
+
+class FFSTError(RuntimeError):
+    """A libffst call returned a status other than FFST_OK."""
+
+    def __init__(self, fn: str, status: int, message: str):
+        super().__init__(f"{fn}: {status_name(status)}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libffst.so (built in-tree by ``build()``) and declare its prototypes."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libffst.so is not built ({path}); run paper_1202_1773_gb300.build.build()")
+        handle = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = handle
+    return _LIB
+
+
+def status_name(status: int) -> str:
+    return lib().ffst_status_string(int(status)).decode()
+
+
+def last_error() -> str:
+    return lib().ffst_last_error().decode()
+
+
+def _check(fn: str, status: int):
+    if status != FFST_OK:
+        raise FFSTError(fn, status, last_error())
+
+
+def _ptr(x) -> int | None:
+    """Device pointer of a tensor-like object, or an int/None passed through."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+# --- C-ABI wrappers (same names as the C entry points) -----------------------
+
+def ffst_plan(rows: int, cols: int, scales: int = 0) -> int:
+    out = _VP()
+    _check("ffst_plan", lib().ffst_plan(int(rows), int(cols), int(scales), ctypes.byref(out)))
+    return out.value
+
+
+def ffst_plan_info(plan: int):
+    r, c, s, n = _I(), _I(), _I(), _I()
+    _check("ffst_plan_info", lib().ffst_plan_info(plan, ctypes.byref(r), ctypes.byref(c), ctypes.byref(s),
+                                                  ctypes.byref(n)))
+    return r.value, c.value, s.value, n.value
+
+
+def ffst_plane_index(plan: int, i: int):
+    cone, j, k = _I(), _I(), _I()
+    _check("ffst_plane_index", lib().ffst_plane_index(plan, int(i), ctypes.byref(cone), ctypes.byref(j),
+                                                      ctypes.byref(k)))
+    return cone.value, j.value, k.value
+
+
+def ffst_spectra(plan: int, psi, stream=None):
+    _check("ffst_spectra", lib().ffst_spectra(plan, _ptr(psi), stream))
+
+
+def ffst_forward(plan: int, img, coeffs, storage: int = FFST_STORE_F32, plane_scale=None, stream=None):
+    _check("ffst_forward", lib().ffst_forward(plan, _ptr(img), _ptr(coeffs), int(storage), _ptr(plane_scale), stream))
+
+
+def ffst_inverse(plan: int, coeffs, storage: int, plane_scale, img, stream=None):
+    _check("ffst_inverse", lib().ffst_inverse(plan, _ptr(coeffs), int(storage), _ptr(plane_scale), _ptr(img), stream))
+
+
+def ffst_adjoint(plan: int, coeffs, storage: int, plane_scale, img, stream=None):
+    _check("ffst_adjoint", lib().ffst_adjoint(plan, _ptr(coeffs), int(storage), _ptr(plane_scale), _ptr(img), stream))
+
+
+def ffst_destroy(plan: int):
+    if plan:
+        lib().ffst_destroy(plan)
+
+
+def ffst_timing_enable(plan: int, enable: bool):
+    _check("ffst_timing_enable", lib().ffst_timing_enable(plan, 1 if enable else 0))
+
+
+def ffst_timing_reset(plan: int):
+    _check("ffst_timing_reset", lib().ffst_timing_reset(plan))
+
+
+def ffst_timing_kinds() -> int:
+    return lib().ffst_timing_kinds()
+
+
+def ffst_timing_read(plan: int, kind: int):
+    name = ctypes.c_char_p()
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    by = ctypes.c_double()
+    _check("ffst_timing_read", lib().ffst_timing_read(plan, int(kind), ctypes.byref(name), ctypes.byref(ms),
+                                                      ctypes.byref(n), ctypes.byref(by)))
+    return name.value.decode(), ms.value, n.value, by.value

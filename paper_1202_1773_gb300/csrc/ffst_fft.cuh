@@ -1,0 +1,178 @@
+// Self-written FFT engine: radix-R DFTs in registers and a register-resident
+// Stockham line FFT whose passes exchange data through shared memory.
+//
+// Layout contract of a line FFT of length L run by a team of T threads:
+// thread t of the team holds v[m] = x[t + T*m], m = 0..E-1 (E = L/T), on
+// entry (natural order input) and v[m] = X[t + T*m] on exit (natural order
+// output).  Consecutive threads therefore touch consecutive elements, so the
+// loads before and the stores after the transform are coalesced.
+//
+// Pass s (radix R, Ns = product of the earlier radices) computes, for every
+// butterfly index j in [0, L/R), the R-point DFT of x[j + r*L/R] after the
+// twiddles W_{Ns R}^{(j mod Ns) r}, and scatters the results to
+// y[(j/Ns) Ns R + (j mod Ns) + r Ns] (the Stockham auto-sort of the FFT
+// literature); the last pass lands exactly in the register layout above.
+#pragma once
+
+#include <type_traits>
+
+#include "ffst_internal.cuh"
+
+namespace ffst {
+
+template <int I, int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+
+// x * W_R^m with W_R = exp(-2 pi i / R) (forward) or its conjugate (inverse).
+// Multiples of pi/4 are special-cased so no multiply by 0 or 1 is emitted.
+template <int R, int m, bool INV>
+__device__ __forceinline__ float2 twiddle_c(float2 x) {
+  constexpr int mm = ((m % R) + R) % R;
+  if constexpr (mm == 0) {
+    return x;
+  } else if constexpr ((8 * mm) % R == 0) {
+    constexpr int o0 = (8 * mm) / R;
+    constexpr int oct = INV ? (8 - o0) % 8 : o0;  // multiply by exp(-i oct pi/4)
+    constexpr float s = 0.70710678118654752440f;
+    if constexpr (oct == 1) return make_float2((x.x + x.y) * s, (x.y - x.x) * s);
+    else if constexpr (oct == 2) return make_float2(x.y, -x.x);
+    else if constexpr (oct == 3) return make_float2((x.y - x.x) * s, -(x.x + x.y) * s);
+    else if constexpr (oct == 4) return make_float2(-x.x, -x.y);
+    else if constexpr (oct == 5) return make_float2(-(x.x + x.y) * s, (x.x - x.y) * s);
+    else if constexpr (oct == 6) return make_float2(-x.y, x.x);
+    else return make_float2((x.x - x.y) * s, (x.x + x.y) * s);
+  } else {
+    constexpr float c = root_cos(mm, R);
+    constexpr float sn = INV ? root_sin(mm, R) : -root_sin(mm, R);
+    return make_float2(x.x * c - x.y * sn, x.x * sn + x.y * c);
+  }
+}
+
+// In-place R-point DFT of x (natural order in and out), R in {1,2,4,8,16,32,64}.
+// R = R1*R2: R1 interleaved DFTs of length R2, twiddles W_R^{n1 k2}, then R2
+// DFTs of length R1 (X[k2 + R2 k1]).
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 (&x)[R]) {
+  if constexpr (R == 1) {
+  } else if constexpr (R == 2) {
+    const float2 a = x[0], b = x[1];
+    x[0] = cadd(a, b);
+    x[1] = csub(a, b);
+  } else if constexpr (R == 4) {
+    const float2 t0 = cadd(x[0], x[2]), t1 = csub(x[0], x[2]);
+    const float2 t2 = cadd(x[1], x[3]), t3 = csub(x[1], x[3]);
+    // (-i) t3 forward, (+i) t3 inverse
+    const float2 r3 = INV ? make_float2(-t3.y, t3.x) : make_float2(t3.y, -t3.x);
+    x[0] = cadd(t0, t2);
+    x[2] = csub(t0, t2);
+    x[1] = cadd(t1, r3);
+    x[3] = csub(t1, r3);
+  } else {
+    constexpr int R1 = (R == 8) ? 2 : ((R == 16 || R == 32) ? 4 : 8);
+    constexpr int R2 = R / R1;
+    float2 y[R1][R2];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) y[n1][n2] = x[n1 + R1 * n2];
+      dft<R2, INV>(y[n1]);
+    }
+    static_for<1, R1>([&](auto n1c) {
+      static_for<1, R2>([&](auto k2c) {
+        constexpr int n1 = decltype(n1c)::value, k2 = decltype(k2c)::value;
+        y[n1][k2] = twiddle_c<R, n1 * k2, INV>(y[n1][k2]);
+      });
+    });
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      float2 z[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) z[n1] = y[n1][k2];
+      dft<R1, INV>(z);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) x[k2 + R2 * k1] = z[k1];
+    }
+  }
+}
+
+// Launch geometry of a line FFT of length L (power of two).
+template <int L>
+struct LCfg {
+  static constexpr int E = (L >= 4096) ? 32 : (L >= 16 ? 16 : L);  // elements per thread
+  static constexpr int T = L / E;                                    // threads per line
+  static constexpr int SH = ilog2(E);                                // one pad slot per E elements
+  static constexpr int BUF = L + (L >> SH) + 2;                      // float2 per team buffer
+  __device__ static __forceinline__ int pad(int i) { return i + (i >> SH); }
+};
+
+// Sync policy.  WARP: every team is a run of <= 32 consecutive threads inside
+// one warp, so a warp barrier orders its shared-memory exchange.  Otherwise
+// (teams larger than a warp, or teams interleaved across warps) the whole
+// CTA synchronises, and every thread of the CTA must run the same passes.
+template <bool WARP>
+__device__ __forceinline__ void team_sync() {
+  if constexpr (WARP) __syncwarp();
+  else __syncthreads();
+}
+
+// Stockham passes starting at sub-transform length Ns.  `tw` holds
+// exp(-2 pi i m / L), m = 0..L-1 (FP64-generated, rounded to FP32).
+// With WARP == false every thread of the CTA must call this uniformly.
+template <int L, bool INV, int Ns, bool WARP>
+__device__ __forceinline__ void stockham(float2 (&v)[LCfg<L>::E], float2* buf, int t,
+                                         const float2* __restrict__ tw) {
+  constexpr int E = LCfg<L>::E, T = LCfg<L>::T;
+  constexpr int REM = L / Ns;
+  constexpr int R = REM >= E ? E : REM;
+  constexpr int B = E / R;  // butterflies per thread in this pass
+  static_assert(E % R == 0, "radix must divide the elements per thread");
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = v[q + B * r];
+    const int j = t + T * q;
+    const int kk = j & (Ns - 1);
+    if constexpr (Ns > 1) {
+      constexpr int STRIDE = L / (Ns * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = __ldg(&tw[kk * r * STRIDE]);
+        if (INV) w.y = -w.y;
+        x[r] = cmul(x[r], w);
+      }
+    }
+    dft<R, INV>(x);
+    if constexpr (Ns * R == L) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q + B * r] = x[r];
+    } else {
+      const int base = (j / Ns) * Ns * R + kk;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[LCfg<L>::pad(base + r * Ns)] = x[r];
+    }
+  }
+  if constexpr (Ns * R < L) {
+    team_sync<WARP>();
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = buf[LCfg<L>::pad(t + T * m)];
+    team_sync<WARP>();
+    stockham<L, INV, Ns * R, WARP>(v, buf, t, tw);
+  }
+}
+
+// Full line FFT (unnormalised).  Forward: X[k] = sum x[n] e^{-2 pi i nk/L};
+// inverse: the same with e^{+2 pi i nk/L}.
+template <int L, bool INV, bool WARP>
+__device__ __forceinline__ void line_fft(float2 (&v)[LCfg<L>::E], float2* buf, int t, const float2* __restrict__ tw) {
+  stockham<L, INV, 1, WARP>(v, buf, t, tw);
+}
+
+}  // namespace ffst

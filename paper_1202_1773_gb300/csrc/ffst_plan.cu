@@ -1,0 +1,361 @@
+// Plan construction: FP64 host tables, plane indexing, spectral supports,
+// plane grouping and workspace; plus the spectra export kernel.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+
+#include "ffst_window.cuh"
+
+namespace ffst {
+
+// ---------------------------------------------------------------------------
+// FP64 window functions for the once-per-plan tables (host only)
+// ---------------------------------------------------------------------------
+// v of Sec. 2.1 eq. (v); the half x > 1/2 uses v(x) = 1 - v(1 - x) (Lemma, Sec. 2.1).
+static double v64(double x) {
+  if (x <= 0.0) return 0.0;
+  if (x >= 1.0) return 1.0;
+  auto p = [](double y) {
+    const double y2 = y * y;
+    return y2 * y2 * (35.0 + y * (-84.0 + y * (70.0 - 20.0 * y)));
+  };
+  return x <= 0.5 ? p(x) : 1.0 - p(1.0 - x);
+}
+
+// psi1_hat in the closed form of Sec. 3.4 (equal to eq. (Psi1) of Sec. 2.1).
+static double psi1_64(double w) {
+  w = std::fabs(w);
+  if (w <= 0.5) return 0.0;
+  if (w < 1.0) return std::sin(0.5 * kPi * v64(2.0 * w - 1.0));
+  if (w <= 2.0) return 1.0;
+  if (w < 4.0) return std::cos(0.5 * kPi * v64(0.5 * w - 1.0));
+  return 0.0;
+}
+
+// varphi of Sec. 2.4.
+static double varphi64(double w) {
+  w = std::fabs(w);
+  if (w <= 0.5) return 1.0;
+  if (w < 1.0) return std::cos(0.5 * kPi * v64(2.0 * w - 1.0));
+  return 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// device kernels used at plan time / for export
+// ---------------------------------------------------------------------------
+
+// For every plane, the smallest and largest half-spectrum column where the
+// spectrum is nonzero (minmax[2i], minmax[2i+1]).
+__global__ void k_support(WinParams w, const PlaneDesc* __restrict__ planes, int eta, int Hc, int* minmax) {
+  const long long per_plane = (long long)w.M * Hc;
+  const long long total = per_plane * eta;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / per_plane);
+    const long long rem = idx - (long long)i * per_plane;
+    const int pr = (int)(rem / Hc), pc = (int)(rem % Hc);
+    const PlaneDesc d = planes[i];
+    if (win_at(w, d, pr, pc) != 0.0f) {
+      atomicMin(&minmax[2 * i], pc);
+      atomicMax(&minmax[2 * i + 1], pc);
+    }
+  }
+}
+
+// psi[i][pr][pc] on the full grid in FFT order; columns beyond N/2 use the
+// point symmetry psi(-omega) = psi(omega) that the Sec. 3.8.1 fix guarantees.
+__global__ void k_spectra(WinParams w, const PlaneDesc* __restrict__ planes, int eta, float* __restrict__ psi) {
+  const long long per_plane = (long long)w.M * w.N;
+  const long long total = per_plane * eta;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / per_plane);
+    const long long rem = idx - (long long)i * per_plane;
+    const int pr = (int)(rem / w.N), pc = (int)(rem % w.N);
+    const PlaneDesc d = planes[i];
+    float val;
+    if (2 * pc <= w.N) val = win_at(w, d, pr, pc);
+    else val = win_at(w, d, (w.M - pr) % w.M, w.N - pc);
+    psi[idx] = val;
+  }
+}
+
+cudaError_t launch_spectra(const ffst_plan_s* p, float* psi, cudaStream_t s) {
+  k_spectra<<<152 * 8, 256, 0, s>>>(p->win, p->d_planes, p->eta, psi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_support(const ffst_plan_s* p, int* d_minmax, cudaStream_t s) {
+  k_support<<<152 * 8, 256, 0, s>>>(p->win, p->d_planes, p->eta, p->Hc, d_minmax);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+ffst_status fail(ffst_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+ffst_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? FFST_ERR_OUT_OF_MEMORY : FFST_ERR_CUDA;
+}
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+static void free_plan(ffst_plan_s* p) {
+  if (!p) return;
+  cudaFree(p->d_planes);
+  cudaFree(p->d_tables);
+  cudaFree(p->d_tw_rows);
+  if (p->d_tw_cols != p->d_tw_rows) cudaFree(p->d_tw_cols);
+  cudaFree(p->d_F);
+  cudaFree(p->d_S);
+  cudaFree(p->d_D);
+  cudaFree(p->d_H);
+  cudaFree(p->d_partials);
+  cudaFree(p->d_items);
+  for (auto& r : p->timer.pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : p->timer.pool) cudaEventDestroy(e);
+  delete p;
+}
+
+// Intermediate budget per plane group.  The column pass writes a group's
+// intermediates and the row pass reads them back; keeping a group within
+// a fraction of the 126 MB L2 lets that round trip stay on chip.
+static long long group_budget_elems() {
+  double mb = 48.0;
+  if (const char* e = std::getenv("FFST_GROUP_MB")) {
+    const double v = std::atof(e);
+    if (v > 0.0) mb = v;
+  }
+  return (long long)(mb * 1024.0 * 1024.0 / sizeof(float2));
+}
+
+static std::vector<float2> twiddles(int L) {
+  std::vector<float2> t(L);
+  for (int m = 0; m < L; ++m) {
+    const double a = 2.0 * kPi * (double)m / (double)L;
+    t[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  return t;
+}
+
+}  // namespace ffst
+
+using namespace ffst;
+
+extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* out) {
+  if (!out) return fail(FFST_ERR_INVALID_ARG, "ffst_plan: out is NULL");
+  *out = nullptr;
+  if (!is_pow2(rows) || !is_pow2(cols) || rows < 8 || cols < 8 || rows > 4096 || cols > 4096)
+    return fail(FFST_ERR_UNSUPPORTED_SIZE, "ffst_plan: rows and cols must be powers of two in [8, 4096], got " +
+                                               std::to_string(rows) + "x" + std::to_string(cols));
+  const int mx = rows > cols ? rows : cols;
+  int lg = 0;
+  while ((1 << (lg + 1)) <= mx) ++lg;
+  const int j0 = scales > 0 ? scales : lg / 2;  // Sec. 3.1: floor(1/2 log2 max(M, N))
+  if (j0 < 1 || j0 > 8)
+    return fail(FFST_ERR_UNSUPPORTED_SIZE, "ffst_plan: scales must be in 1..8, got " + std::to_string(j0));
+
+  std::unique_ptr<ffst_plan_s, void (*)(ffst_plan_s*)> p(new ffst_plan_s, free_plan);
+  cudaGetDevice(&p->device);
+  p->M = rows;
+  p->N = cols;
+  p->j0 = j0;
+  p->eta = (1 << (j0 + 2)) - 3;  // Sec. 3.5.2
+  p->Hc = cols / 2 + 1;
+  p->hm = rows / 2;
+  p->hn = cols / 2;
+
+  // plane table, Sec. 3.5.2: low-pass, then per scale counter-clockwise
+  p->planes.clear();
+  auto add = [&](int kappa, int j, int k) {
+    PlaneDesc d{};
+    d.kappa = kappa;
+    d.j = j;
+    d.k = k;
+    p->planes.push_back(d);
+  };
+  add(kLowpass, -1, 0);
+  for (int j = 0; j < j0; ++j) {
+    const int J = 1 << j;
+    add(kH, j, 0);
+    for (int k = -1; k > -J; --k) add(kH, j, k);
+    add(kSeam, j, -J);
+    for (int k = -J + 1; k < J; ++k) add(kV, j, k);
+    add(kSeam, j, J);
+    for (int k = J - 1; k > 0; --k) add(kH, j, k);
+  }
+  if ((int)p->planes.size() != p->eta) return fail(FFST_ERR_INVALID_ARG, "ffst_plan: internal plane count mismatch");
+
+  // FP64 window tables (Sec. 3.5.1 grid: xi = a * X / floor(L/2), X = 2^{2 j0 - 1})
+  const double X = std::ldexp(1.0, 2 * j0 - 1);
+  const double dc = X / p->hn, dr = X / p->hm;
+  const int ncol = p->hn + 1, nrow = p->hm + 1;
+  std::vector<float> tab((size_t)j0 * ncol + (size_t)j0 * nrow + ncol + nrow);
+  float* psi1_col = tab.data();
+  float* psi1_row = psi1_col + (size_t)j0 * ncol;
+  float* phi_col = psi1_row + (size_t)j0 * nrow;
+  float* phi_row = phi_col + ncol;
+  for (int j = 0; j < j0; ++j) {
+    const double a = std::ldexp(1.0, -2 * j);  // a_j = 4^-j
+    for (int q = 0; q < ncol; ++q) psi1_col[(size_t)j * ncol + q] = (float)psi1_64(a * q * dc);
+    for (int q = 0; q < nrow; ++q) psi1_row[(size_t)j * nrow + q] = (float)psi1_64(a * q * dr);
+  }
+  for (int q = 0; q < ncol; ++q) phi_col[q] = (float)varphi64(q * dc);
+  for (int q = 0; q < nrow; ++q) phi_row[q] = (float)varphi64(q * dr);
+
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->d_tables, tab.size() * sizeof(float))) != cudaSuccess) return cuda_fail(e, "ffst_plan tables");
+  if ((e = cudaMemcpy(p->d_tables, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "ffst_plan tables upload");
+  p->win.M = rows;
+  p->win.N = cols;
+  p->win.hm = p->hm;
+  p->win.hn = p->hn;
+  p->win.psi1_col = p->d_tables;
+  p->win.psi1_row = p->d_tables + (size_t)j0 * ncol;
+  p->win.phi_col = p->win.psi1_row + (size_t)j0 * nrow;
+  p->win.phi_row = p->win.phi_col + ncol;
+
+  // twiddles (FP64 -> FP32)
+  {
+    auto tr = twiddles(cols);
+    if ((e = cudaMalloc(&p->d_tw_rows, tr.size() * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "twiddles");
+    cudaMemcpy(p->d_tw_rows, tr.data(), tr.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (rows == cols) {
+      p->d_tw_cols = p->d_tw_rows;
+    } else {
+      auto tc = twiddles(rows);
+      if ((e = cudaMalloc(&p->d_tw_cols, tc.size() * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "twiddles");
+      cudaMemcpy(p->d_tw_cols, tc.data(), tc.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    }
+  }
+
+  // supports
+  if ((e = cudaMalloc(&p->d_planes, p->planes.size() * sizeof(PlaneDesc))) != cudaSuccess)
+    return cuda_fail(e, "plane descriptors");
+  cudaMemcpy(p->d_planes, p->planes.data(), p->planes.size() * sizeof(PlaneDesc), cudaMemcpyHostToDevice);
+  {
+    std::vector<int> mm(2 * p->eta);
+    for (int i = 0; i < p->eta; ++i) {
+      mm[2 * i] = INT_MAX;
+      mm[2 * i + 1] = -1;
+    }
+    int* d_mm = nullptr;
+    if ((e = cudaMalloc(&d_mm, mm.size() * sizeof(int))) != cudaSuccess) return cuda_fail(e, "support scratch");
+    cudaMemcpy(d_mm, mm.data(), mm.size() * sizeof(int), cudaMemcpyHostToDevice);
+    e = launch_support(p.get(), d_mm, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(mm.data(), d_mm, mm.size() * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d_mm);
+    if (e != cudaSuccess) return cuda_fail(e, "ffst_plan support kernel");
+    for (int i = 0; i < p->eta; ++i) {
+      if (mm[2 * i + 1] < 0) {
+        p->planes[i].c0 = 0;
+        p->planes[i].W = 0;
+      } else {
+        p->planes[i].c0 = mm[2 * i];
+        p->planes[i].W = mm[2 * i + 1] - mm[2 * i] + 1;
+      }
+    }
+  }
+
+  // groups and forward column work items
+  const long long budget = group_budget_elems();
+  const int P = cols_per_cta(rows);
+  std::vector<ColItem> items;
+  {
+    Group g{0, 0, 0, 0, 0};
+    long long maxg = 0;
+    for (int i = 0; i < p->eta; ++i) {
+      const long long el = (long long)rows * p->planes[i].W;
+      if (g.p1 > g.p0 && g.elems + el > budget) {
+        g.nitems = (int)items.size() - g.item0;
+        p->groups.push_back(g);
+        maxg = std::max(maxg, g.elems);
+        g = Group{i, i, 0, (int)items.size(), 0};
+      }
+      p->planes[i].off = g.elems;
+      p->planes[i].item0 = (int)items.size();
+      for (int c = p->planes[i].c0; c < p->planes[i].c0 + p->planes[i].W; c += P) items.push_back(ColItem{i, c});
+      p->planes[i].nitems = (int)items.size() - p->planes[i].item0;
+      g.elems += el;
+      g.p1 = i + 1;
+    }
+    g.nitems = (int)items.size() - g.item0;
+    p->groups.push_back(g);
+    maxg = std::max(maxg, g.elems);
+    p->h_elems = maxg;
+  }
+  p->total_items = (int)items.size();
+  cudaMemcpy(p->d_planes, p->planes.data(), p->planes.size() * sizeof(PlaneDesc), cudaMemcpyHostToDevice);
+  if (!items.empty()) {
+    if ((e = cudaMalloc(&p->d_items, items.size() * sizeof(ColItem))) != cudaSuccess) return cuda_fail(e, "items");
+    cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(ColItem), cudaMemcpyHostToDevice);
+    if ((e = cudaMalloc(&p->d_partials, items.size() * sizeof(float))) != cudaSuccess) return cuda_fail(e, "partials");
+  }
+
+  // workspace
+  const size_t spec = (size_t)rows * p->Hc;
+  if ((e = cudaMalloc(&p->d_F, spec * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "workspace F");
+  if ((e = cudaMalloc(&p->d_S, spec * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "workspace S");
+  if ((e = cudaMalloc(&p->d_D, spec * sizeof(float))) != cudaSuccess) return cuda_fail(e, "workspace D");
+  if (p->h_elems > 0 && (e = cudaMalloc(&p->d_H, (size_t)p->h_elems * sizeof(float2))) != cudaSuccess)
+    return cuda_fail(e, "workspace H");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "ffst_plan");
+  *out = p.release();
+  return FFST_OK;
+}
+
+extern "C" ffst_status ffst_plan_info(ffst_plan_t plan, int* rows, int* cols, int* scales, int* num_planes) {
+  if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_info: plan is NULL");
+  if (rows) *rows = plan->M;
+  if (cols) *cols = plan->N;
+  if (scales) *scales = plan->j0;
+  if (num_planes) *num_planes = plan->eta;
+  return FFST_OK;
+}
+
+extern "C" ffst_status ffst_plane_index(ffst_plan_t plan, int i, int* cone, int* j, int* k) {
+  if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plane_index: plan is NULL");
+  if (i < 0 || i >= plan->eta) return fail(FFST_ERR_INVALID_ARG, "ffst_plane_index: index out of range");
+  const PlaneDesc& d = plan->planes[i];
+  if (cone) *cone = d.kappa;
+  if (j) *j = d.j;
+  if (k) *k = d.k;
+  return FFST_OK;
+}
+
+extern "C" void ffst_destroy(ffst_plan_t plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  free_plan(plan);
+}
+
+extern "C" const char* ffst_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* ffst_status_string(int status) {
+  switch (status) {
+    case FFST_OK: return "FFST_OK";
+    case FFST_ERR_INVALID_ARG: return "FFST_ERR_INVALID_ARG";
+    case FFST_ERR_UNSUPPORTED_SIZE: return "FFST_ERR_UNSUPPORTED_SIZE";
+    case FFST_ERR_OUT_OF_MEMORY: return "FFST_ERR_OUT_OF_MEMORY";
+    case FFST_ERR_CUDA: return "FFST_ERR_CUDA";
+    case FFST_ERR_TIMEOUT: return "FFST_ERR_TIMEOUT";
+    default: return "FFST_ERR_UNKNOWN";
+  }
+}

@@ -1,0 +1,88 @@
+// In-register generator of the shearlet spectra psi_hat_i (FP32).
+//
+// Definitions (arXiv:1202.1773):
+//   v          Sec. 2.1 eq. (v)      polynomial piece p(x) = x^4 (35 - 84x + 70x^2 - 20x^3)
+//   psi2_hat   Sec. 2.1 eq. (Psi2)   sqrt(v(1 - |u|)), zero for |u| >= 1
+//   psi1_hat   Sec. 2.1 eq. (Psi1)   per-scale 1-D table, FP64-generated on the host
+//   varphi     Sec. 2.4              1-D table, FP64-generated on the host
+//   cones      Sec. 2.3              exact integer test on the frequency indices
+//   spectra    Sec. 3.1 eq. (shearletTransform), glued seam shearlets for |k| = 2^j
+//   grid       Sec. 3.5.1            xi = omega * X / floor(L/2) per axis, X = 2^{2 j0 - 1}
+//   fix        Sec. 3.8.1            Nyquist row/column mirrored, squares averaged
+//
+// Accuracy notes.  The shear argument u = 2^j xi2/xi1 + k (h cone) is formed
+// as one fraction of exact integers, (2^j o2 floor(N/2) + k o1 floor(M/2)) /
+// (o1 floor(M/2)), so the cancellation against k happens exactly and u has
+// FP32 relative accuracy on the support |u| < 1.  v near 1 is evaluated as
+// 1 - p(1 - x) (the symmetry v(x) + v(1-x) = 1 of Sec. 2.1), so
+// psi2 keeps ~1 ulp absolute accuracy near its peak.
+#pragma once
+
+#include "ffst_internal.cuh"
+
+namespace ffst {
+
+__device__ __forceinline__ float vpoly(float x) {
+  const float x2 = x * x;
+  return x2 * x2 * fmaf(x, fmaf(x, fmaf(x, -20.0f, 70.0f), -84.0f), 35.0f);
+}
+
+__device__ __forceinline__ float psi2_hat(float u) {
+  const float y = fabsf(u);
+  if (y >= 1.0f) return 0.0f;
+  const float vv = (y < 0.5f) ? 1.0f - vpoly(y) : vpoly(1.0f - y);
+  return sqrtf(vv);
+}
+
+// Unfixed spectrum of plane (kappa, j, k) at integer frequency (o2, o1).
+// |o1| <= floor(N/2), |o2| <= floor(M/2), M, N <= 4096 and j <= 7 keep every
+// product below 2^31.
+__device__ __forceinline__ float win_raw(const WinParams& w, int kappa, int j, int k, int o2, int o1) {
+  const int a2 = abs(o2), a1 = abs(o1);
+  const int lhs = a2 * w.hn;  // |xi2| ~ lhs, |xi1| ~ rhs (common factor X/(hm hn))
+  const int rhs = a1 * w.hm;
+  if (kappa == kLowpass) return (lhs <= rhs) ? __ldg(&w.phi_col[a1]) : __ldg(&w.phi_row[a2]);
+  bool use_h;
+  if (lhs < rhs) {
+    use_h = true;
+  } else if (lhs > rhs) {
+    use_h = false;
+  } else {
+    // seam line |xi1| = |xi2| (or the origin): only the glued seam shearlet, h formula
+    if (kappa != kSeam || (a1 | a2) == 0) return 0.0f;
+    use_h = true;
+  }
+  if ((use_h && kappa == kV) || (!use_h && kappa == kH)) return 0.0f;
+  float p1;
+  int num, den;
+  if (use_h) {
+    p1 = __ldg(&w.psi1_col[j * (w.hn + 1) + a1]);
+    num = (1 << j) * o2 * w.hn + k * o1 * w.hm;
+    den = o1 * w.hm;
+  } else {
+    p1 = __ldg(&w.psi1_row[j * (w.hm + 1) + a2]);
+    num = (1 << j) * o1 * w.hm + k * o2 * w.hn;
+    den = o2 * w.hn;
+  }
+  if (p1 == 0.0f) return 0.0f;
+  const float u = __int2float_rn(num) / __int2float_rn(den);
+  return p1 * psi2_hat(u);
+}
+
+// Spectrum with the Sec. 3.8.1 fix at half-spectrum position (pr, pc):
+// pr in [0, M) (omega_2 in FFT order), pc in [0, N/2] (omega_1 >= 0, and
+// -N/2 at pc = N/2).  On the Nyquist row (or column) the value is
+// sqrt((psi(w)^2 + psi(w')^2)/2) with w' the point mirrored across the axis;
+// the corner (-M/2, -N/2) is its own conjugate partner and stays unchanged.
+__device__ __forceinline__ float win_at(const WinParams& w, const PlaneDesc& d, int pr, int pc) {
+  const int o2 = (2 * pr < w.M) ? pr : pr - w.M;
+  const int o1 = (2 * pc < w.N) ? pc : pc - w.N;
+  const bool nyq_r = (w.M % 2 == 0) && (2 * pr == w.M);
+  const bool nyq_c = (w.N % 2 == 0) && (2 * pc == w.N);
+  const float a = win_raw(w, d.kappa, d.j, d.k, o2, o1);
+  if (nyq_r == nyq_c) return a;
+  const float b = nyq_r ? win_raw(w, d.kappa, d.j, d.k, -o2, o1) : win_raw(w, d.kappa, d.j, d.k, o2, -o1);
+  return sqrtf(0.5f * (a * a + b * b));
+}
+
+}  // namespace ffst

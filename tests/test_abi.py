@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads and exports every entry point of include/ffst.h.
+
+Host-side argument checks are exercised too: these calls return before any
+CUDA work, so they run without a GPU.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1202_1773_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "ffst.h")) as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ffst_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+    # and the binding declares a prototype for each of them
+    bound = {n for n, _, _ in _lib.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def test_status_strings(lib):
+    assert _lib.status_name(0) == "FFST_OK"
+    assert _lib.status_name(2) == "FFST_ERR_UNSUPPORTED_SIZE"
+    assert _lib.status_name(99) == "FFST_ERR_UNKNOWN"
+
+
+@pytest.mark.parametrize("rows,cols,scales", [(0, 64, 0), (64, 0, 0), (48, 64, 0), (64, 100, 0),
+                                              (4, 64, 0), (64, 8192, 0), (64, 64, 9)])
+def test_unsupported_sizes_rejected_on_host(lib, rows, cols, scales):
+    out = ctypes.c_void_p()
+    st = lib.ffst_plan(rows, cols, scales, ctypes.byref(out))
+    assert st == _lib.FFST_ERR_UNSUPPORTED_SIZE
+    assert out.value is None
+    assert "ffst_plan" in _lib.last_error()
+
+
+def test_null_arguments_rejected_on_host(lib):
+    assert lib.ffst_plan(64, 64, 0, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_plan_info(None, None, None, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_plane_index(None, 0, None, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_forward(None, None, None, 0, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_inverse(None, None, 0, None, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_adjoint(None, None, 0, None, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_spectra(None, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_timing_enable(None, 1) == _lib.FFST_ERR_INVALID_ARG
+    lib.ffst_destroy(None)  # no-op
+    with pytest.raises(_lib.FFSTError):
+        _lib.ffst_plan(64, 48, 0)
