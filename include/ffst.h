@@ -126,6 +126,26 @@ ffst_status ffst_inverse(ffst_plan_t plan, const void* coeffs, int storage,
 ffst_status ffst_adjoint(ffst_plan_t plan, const void* coeffs, int storage,
                          const float* plane_scale, float* img, void* stream);
 
+/*
+ * Forward transform for small images that allocates nothing (the paper has
+ * no counterpart; it exists for callers that cannot call cudaMalloc, such as
+ * code running during CUDA stream capture, processes whose framework has
+ * reserved nearly all device memory, or hosts that forbid allocation after
+ * start-up; ffst_plan allocates, so those callers cannot build a plan).
+ *   rows, cols:  powers of two in [8, 256]; scales in 1..4 (<= 0: default j0).
+ *                Anything larger returns FFST_ERR_UNSUPPORTED_SIZE before any
+ *                work is enqueued.
+ *   img:         device, rows x cols float32, read only.
+ *   coeffs:      device, [eta][rows][cols] float32, fully overwritten.
+ * Same result as ffst_forward with FFST_STORE_F32 (to FP32 rounding).  All
+ * tables and intermediates live in one static device array of about 2.5 MB
+ * that every GPU loading the library holds until the process exits.  The
+ * first call on a device looks up that array's address (and may load the
+ * module), so make it before any stream capture.  Calls share the array:
+ * two calls whose work overlaps on the GPU race and corrupt each other.
+ */
+ffst_status ffst_forward_noalloc(int rows, int cols, int scales, const float* img, float* coeffs, void* stream);
+
 /* Free a plan and everything it owns (synchronises the device first).  NULL is a no-op. */
 void ffst_destroy(ffst_plan_t plan);
 

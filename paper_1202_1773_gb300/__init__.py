@@ -31,6 +31,7 @@ from ._lib import (  # noqa: F401
     ffst_adjoint,
     ffst_destroy,
     ffst_forward,
+    ffst_forward_noalloc,
     ffst_inverse,
     ffst_plan,
     ffst_plan_info,

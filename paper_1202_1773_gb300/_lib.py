@@ -37,6 +37,7 @@ SIGNATURES = [
     ("ffst_forward", _I, [_VP, _VP, _VP, _I, _VP, _VP]),
     ("ffst_inverse", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
     ("ffst_adjoint", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
+    ("ffst_forward_noalloc", _I, [_I, _I, _I, _VP, _VP, _VP]),
     ("ffst_destroy", None, [_VP]),
     ("ffst_last_error", ctypes.c_char_p, []),
     ("ffst_status_string", ctypes.c_char_p, [_I]),
@@ -136,6 +137,12 @@ def ffst_inverse(plan: int, coeffs, storage: int, plane_scale, img, stream=None)
 
 def ffst_adjoint(plan: int, coeffs, storage: int, plane_scale, img, stream=None):
     _check("ffst_adjoint", lib().ffst_adjoint(plan, _ptr(coeffs), int(storage), _ptr(plane_scale), _ptr(img), stream))
+
+
+def ffst_forward_noalloc(rows: int, cols: int, scales: int, img, coeffs, stream=None):
+    """Allocation-free forward transform of a small image (see include/ffst.h)."""
+    _check("ffst_forward_noalloc", lib().ffst_forward_noalloc(int(rows), int(cols), int(scales), _ptr(img),
+                                                              _ptr(coeffs), stream))
 
 
 def ffst_destroy(plan: int):
