@@ -60,7 +60,9 @@ class FFSTError(RuntimeError):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library to load: ``FFST_LIB_PATH`` if set (a tagged variant
+    build), else the default in-tree build."""
+    return os.environ.get("FFST_LIB_PATH") or _build.LIB
 
 
 def lib() -> ctypes.CDLL:

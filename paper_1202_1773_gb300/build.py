@@ -20,6 +20,13 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libffst.so")
+
+
+def variant_dir(tag: str | None) -> str:
+    """Build directory of a tagged variant (``_build_<tag>``), or the default."""
+    return BUILD if not tag else os.path.join(PKG, "_build_" + tag)
+
+
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -46,16 +53,22 @@ def _stale(obj: str, src: str, hdr_mtime: float) -> bool:
     return m < os.path.getmtime(src) or m < hdr_mtime
 
 
-def build(verbose: bool = False, extra_flags=(), jobs: int | None = None) -> str:
-    """Compile and link libffst.so; return its path."""
+def build(verbose: bool = False, extra_flags=(), jobs: int | None = None, tag: str | None = None) -> str:
+    """Compile and link libffst.so; return its path.
+
+    ``extra_flags`` (e.g. ``-DFFST_ROW_E_LONG=16``) with a ``tag`` build a
+    variant into its own directory, loadable through ``FFST_LIB_PATH``.
+    """
     nvcc = nvcc_path()
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = variant_dir(tag)
+    lib_path = os.path.join(bdir, "libffst.so")
+    os.makedirs(bdir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_mtime = max([os.path.getmtime(h) for h in _headers()] + [0.0])
     flags = _flags(extra_flags)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         if not _stale(obj, src, hdr_mtime):
             return obj, None
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
@@ -73,12 +86,12 @@ def build(verbose: bool = False, extra_flags=(), jobs: int | None = None) -> str
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     objs = [o for o, _ in results]
-    if not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        cmd = [nvcc] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"]
+    if not os.path.exists(lib_path) or any(os.path.getmtime(o) > os.path.getmtime(lib_path) for o in objs):
+        cmd = [nvcc] + ARCH + ["-shared", "-o", lib_path] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n$ " + " ".join(cmd) + "\n" + r.stdout + r.stderr)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
@@ -86,5 +99,12 @@ if __name__ == "__main__":
     import time
 
     t0 = time.time()
-    path = build(verbose="-v" in sys.argv)
+    tag = None
+    flags = []
+    for a in sys.argv[1:]:
+        if a.startswith("--tag="):
+            tag = a.split("=", 1)[1]
+        elif a.startswith("-D"):
+            flags.append(a)
+    path = build(verbose="-v" in sys.argv, extra_flags=flags, tag=tag)
     print(f"built {path} in {time.time() - t0:.1f}s")

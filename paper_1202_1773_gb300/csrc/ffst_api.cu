@@ -1,7 +1,14 @@
 // Transforms (forward / inverse / adjoint / spectra export) and kernel timers.
+//
+// Schedule of one transform on a plan with plane groups g = 0..G-1 (each
+// group's column-pass intermediate fits in L2; two buffers alternate):
+//   forward:  fft2(img) -> F;  cols(0);  [cols(g) | rows(g-1)] for g = 1..G-1;  rows(G-1)
+//   inverse:  S = 0;  rows(0);  [rows(g) | cols(g-1)] for g = 1..G-1;  cols(G-1);  ifft2(S)
+// where [a | b] is one fused launch whose blocks interleave both passes
+// (square images); other sizes run the same passes as separate launches.
 #include <cstring>
 
-#include "ffst_internal.cuh"
+#include "ffst_kernels.cuh"
 
 namespace ffst {
 
@@ -28,9 +35,9 @@ static cudaError_t timed(ffst_plan_s* p, int kind, double bytes, cudaStream_t s,
   return e;
 }
 
-static const char* kKindNames[kTimeKinds] = {"img_rows_r2c", "img_cols_fft", "fwd_cols", "fwd_rows_c2r",
+static const char* kKindNames[kTimeKinds] = {"img_rows_r2c", "img_cols_fft", "fwd_cols",      "fwd_rows_c2r",
                                              "inv_rows_r2c", "inv_cols",     "out_cols_ifft", "out_rows_c2r",
-                                             "other"};
+                                             "fwd_fused",    "inv_fused",    "other"};
 
 static ffst_status check_storage(int storage, const float* scale, const char* fn) {
   if (storage != FFST_STORE_F32 && storage != FFST_STORE_F16 && storage != FFST_STORE_BF16)
@@ -40,29 +47,210 @@ static ffst_status check_storage(int storage, const float* scale, const char* fn
   return FFST_OK;
 }
 
+static float2* hbuf(const ffst_plan_s* p, size_t g) { return p->d_H + (g % 2) * p->h_elems; }
+
+static FwdColsArgs fwd_cols_args(const ffst_plan_s* p, const Group& g, float2* H, float* partials) {
+  FwdColsArgs a;
+  a.F = p->d_F;
+  a.Hc = p->Hc;
+  a.planes = p->d_planes;
+  a.items = p->d_items + g.item0;
+  a.rng = p->d_rng;
+  a.H = H;
+  a.w = p->win;
+  a.tw = p->d_tw_cols;
+  a.partials = partials ? partials + g.item0 : nullptr;
+  return a;
+}
+
+static C2RArgs plane_c2r_args(const ffst_plan_s* p, const Group& g, const float2* H, void* coeffs, int storage,
+                              const float* plane_scale) {
+  const long long plane = (long long)p->M * p->N;
+  C2RArgs a;
+  a.src = H;
+  a.planes = p->d_planes;
+  a.c0 = 0;
+  a.W = 0;
+  a.ld = 0;
+  a.M = p->M;
+  a.plane0 = g.p0;
+  a.dst = static_cast<char*>(coeffs) + (long long)g.p0 * plane * (storage == FFST_STORE_F32 ? 4 : 2);
+  a.dst_plane_stride = plane;
+  a.st = storage;
+  a.plane_scale = plane_scale;
+  a.scale = 1.0f / (float)plane;
+  a.tw = p->d_tw_rows;
+  a.rtw = p->d_rtw;
+  return a;
+}
+
+static R2CArgs plane_r2c_args(const ffst_plan_s* p, const Group& g, const void* coeffs, int storage,
+                              const float* plane_scale, float2* H) {
+  const long long plane = (long long)p->M * p->N;
+  R2CArgs a;
+  a.src = static_cast<const char*>(coeffs) + (long long)g.p0 * plane * (storage == FFST_STORE_F32 ? 4 : 2);
+  a.src_plane_stride = plane;
+  a.st = storage;
+  a.plane_scale = plane_scale;
+  a.plane0 = g.p0;
+  a.M = p->M;
+  a.dst = H;
+  a.planes = p->d_planes;
+  a.c0 = 0;
+  a.W = 0;
+  a.ld = 0;
+  a.tw = p->d_tw_rows;
+  a.rtw = p->d_rtw;
+  return a;
+}
+
+static InvColsArgs inv_cols_args(const ffst_plan_s* p, const Group& g, const float2* H) {
+  InvColsArgs a;
+  a.H = H;
+  a.Hc = p->Hc;
+  a.planes = p->d_planes;
+  a.p0 = g.p0;
+  a.p1 = g.p1;
+  a.rng = p->d_rng;
+  a.S = p->d_S;
+  a.w = p->win;
+  a.tw = p->d_tw_cols;
+  return a;
+}
+
+static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int storage, float* plane_scale,
+                            cudaStream_t s) {
+  const long long plane = (long long)p->M * p->N;
+  const int esz = storage == FFST_STORE_F32 ? 4 : 2;
+  const int Lr = p->N / 2;
+  cudaError_t e;
+  // fft2 of the image: row R2C into F, then column FFT in place
+  R2CArgs ia;
+  std::memset(&ia, 0, sizeof(ia));
+  ia.src = img;
+  ia.st = FFST_STORE_F32;
+  ia.M = p->M;
+  ia.dst = p->d_F;
+  ia.c0 = 0;
+  ia.W = p->Hc;
+  ia.ld = p->Hc;
+  ia.tw = p->d_tw_rows;
+  ia.rtw = p->d_rtw;
+  e = timed(p, kTimeImgRows, 4.0 * plane, s, [&] { return launch_rows_r2c(Lr, ia, 1, s); });
+  if (e != cudaSuccess) return cuda_fail(e, "forward image row pass");
+  e = timed(p, kTimeImgCols, 0.0, s,
+            [&] { return launch_cols_fft(p->M, p->d_F, p->Hc, p->Hc, false, nullptr, p->d_tw_cols, s); });
+  if (e != cudaSuccess) return cuda_fail(e, "forward image column pass");
+
+  float* partials = storage == FFST_STORE_F32 ? nullptr : p->d_partials;
+  // F16 stores c_i * s_i with max |c_i s_i| <= 2^15 < 65504; BF16 normalises to <= 1
+  const float target = storage == FFST_STORE_F16 ? 32768.0f : 1.0f;
+  auto scales = [&](size_t gi) -> cudaError_t {
+    if (!partials) return cudaSuccess;
+    return timed(p, kTimeOther, 0.0, s,
+                 [&] { return launch_plane_scales(p, p->groups[gi], partials, target, plane_scale, s); });
+  };
+  const size_t G = p->groups.size();
+  if (fused_supported(p->M, p->N)) {
+    e = timed(p, kTimeFwdCols, 0.0, s, [&] {
+      return launch_fwd_cols(p->M, fwd_cols_args(p, p->groups[0], hbuf(p, 0), partials), p->groups[0].nitems, s);
+    });
+    if (e == cudaSuccess) e = scales(0);
+    for (size_t g = 1; g < G && e == cudaSuccess; ++g) {
+      const Group& cg = p->groups[g];
+      const Group& rg = p->groups[g - 1];
+      const double by = (double)(rg.p1 - rg.p0) * plane * esz;
+      e = timed(p, kTimeFwdFused, by, s, [&] {
+        return launch_fwd_fused(p->M, fwd_cols_args(p, cg, hbuf(p, g), partials), cg.nitems,
+                                plane_c2r_args(p, rg, hbuf(p, g - 1), coeffs, storage, plane_scale), rg.p1 - rg.p0,
+                                s);
+      });
+      if (e == cudaSuccess) e = scales(g);
+    }
+    if (e == cudaSuccess) {
+      const Group& rg = p->groups[G - 1];
+      e = timed(p, kTimeFwdRows, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
+        return launch_rows_c2r(Lr, plane_c2r_args(p, rg, hbuf(p, G - 1), coeffs, storage, plane_scale),
+                               rg.p1 - rg.p0, s);
+      });
+    }
+  } else {
+    for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
+      const Group& gr = p->groups[g];
+      e = timed(p, kTimeFwdCols, 0.0, s, [&] {
+        return launch_fwd_cols(p->M, fwd_cols_args(p, gr, hbuf(p, 0), partials), gr.nitems, s);
+      });
+      if (e == cudaSuccess) e = scales(g);
+      if (e == cudaSuccess)
+        e = timed(p, kTimeFwdRows, (double)(gr.p1 - gr.p0) * plane * esz, s, [&] {
+          return launch_rows_c2r(Lr, plane_c2r_args(p, gr, hbuf(p, 0), coeffs, storage, plane_scale), gr.p1 - gr.p0,
+                                 s);
+        });
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "forward plane passes");
+  return FFST_OK;
+}
+
 static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, const float* plane_scale, float* img,
                              cudaStream_t s, bool normalise) {
   const long long plane = (long long)p->M * p->N;
   const int esz = storage == FFST_STORE_F32 ? 4 : 2;
-  cudaError_t e;
-  for (size_t gi = 0; gi < p->groups.size(); ++gi) {
-    const Group& g = p->groups[gi];
-    const int n = g.p1 - g.p0;
-    e = timed(p, kTimeInvRows, (double)n * plane * esz, s, [&] {
-      return launch_rows_r2c(p, p->N, static_cast<const char*>(coeffs) + (long long)g.p0 * plane * esz, storage,
-                             plane_scale, g.p0, n, plane, p->d_H, true, 0, 0, 0, s);
-    });
-    if (e != cudaSuccess) return cuda_fail(e, "inverse row pass");
-    e = timed(p, kTimeInvCols, 0.0, s, [&] { return launch_inv_cols(p, p->M, g, gi == 0, s); });
-    if (e != cudaSuccess) return cuda_fail(e, "inverse column pass");
+  const int Lr = p->N / 2;
+  const int npanels = (p->Hc + cols_per_cta(p->M) - 1) / cols_per_cta(p->M);
+  cudaError_t e = cudaMemsetAsync(p->d_S, 0, sizeof(float2) * (size_t)p->M * p->Hc, s);
+  if (e != cudaSuccess) return cuda_fail(e, "inverse accumulator clear");
+  const size_t G = p->groups.size();
+  if (fused_supported(p->M, p->N)) {
+    {
+      const Group& rg = p->groups[0];
+      e = timed(p, kTimeInvRows, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
+        return launch_rows_r2c(Lr, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, 0)), rg.p1 - rg.p0,
+                               s);
+      });
+    }
+    for (size_t g = 1; g < G && e == cudaSuccess; ++g) {
+      const Group& rg = p->groups[g];
+      const Group& cg = p->groups[g - 1];
+      e = timed(p, kTimeInvFused, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
+        return launch_inv_fused(p->M, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, g)), rg.p1 - rg.p0,
+                                inv_cols_args(p, cg, hbuf(p, g - 1)), npanels, s);
+      });
+    }
+    if (e == cudaSuccess)
+      e = timed(p, kTimeInvCols, 0.0, s, [&] {
+        return launch_inv_cols(p->M, inv_cols_args(p, p->groups[G - 1], hbuf(p, G - 1)), npanels, s);
+      });
+  } else {
+    for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
+      const Group& gr = p->groups[g];
+      e = timed(p, kTimeInvRows, (double)(gr.p1 - gr.p0) * plane * esz, s, [&] {
+        return launch_rows_r2c(Lr, plane_r2c_args(p, gr, coeffs, storage, plane_scale, hbuf(p, 0)), gr.p1 - gr.p0,
+                               s);
+      });
+      if (e == cudaSuccess)
+        e = timed(p, kTimeInvCols, 0.0, s,
+                  [&] { return launch_inv_cols(p->M, inv_cols_args(p, gr, hbuf(p, 0)), npanels, s); });
+    }
   }
-  e = timed(p, kTimeOutCols, 0.0, s,
-            [&] { return launch_cols_fft(p, p->M, p->d_S, p->Hc, p->Hc, true, normalise ? p->d_D : nullptr, s); });
-  if (e != cudaSuccess) return cuda_fail(e, "inverse final column pass");
-  e = timed(p, kTimeOutRows, 4.0 * plane, s, [&] {
-    return launch_rows_c2r(p, p->N, p->d_S, false, p->Hc, p->Hc, 0, 1, img, FFST_STORE_F32, nullptr, 0,
-                           1.0f / (float)plane, s);
+  if (e != cudaSuccess) return cuda_fail(e, "inverse plane passes");
+  e = timed(p, kTimeOutCols, 0.0, s, [&] {
+    return launch_cols_fft(p->M, p->d_S, p->Hc, p->Hc, true, normalise ? p->d_invD : nullptr, p->d_tw_cols, s);
   });
+  if (e != cudaSuccess) return cuda_fail(e, "inverse final column pass");
+  C2RArgs oa;
+  std::memset(&oa, 0, sizeof(oa));
+  oa.src = p->d_S;
+  oa.c0 = 0;
+  oa.W = p->Hc;
+  oa.ld = p->Hc;
+  oa.M = p->M;
+  oa.dst = img;
+  oa.st = FFST_STORE_F32;
+  oa.scale = 1.0f / (float)plane;
+  oa.tw = p->d_tw_rows;
+  oa.rtw = p->d_rtw;
+  e = timed(p, kTimeOutRows, 4.0 * plane, s, [&] { return launch_rows_c2r(Lr, oa, 1, s); });
   if (e != cudaSuccess) return cuda_fail(e, "inverse final row pass");
   return FFST_OK;
 }
@@ -84,37 +272,7 @@ extern "C" ffst_status ffst_forward(ffst_plan_t plan, const float* img, void* co
   if (!plan || !img || !coeffs) return fail(FFST_ERR_INVALID_ARG, "ffst_forward: NULL argument");
   ffst_status st = check_storage(storage, plane_scale, "ffst_forward");
   if (st != FFST_OK) return st;
-  ffst_plan_s* p = plan;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const long long plane = (long long)p->M * p->N;
-  const int esz = storage == FFST_STORE_F32 ? 4 : 2;
-  cudaError_t e;
-  // fft2 of the image: row R2C into F, then column FFT in place
-  e = timed(p, kTimeImgRows, 4.0 * plane, s, [&] {
-    return launch_rows_r2c(p, p->N, img, FFST_STORE_F32, nullptr, 0, 1, 0, p->d_F, false, 0, p->Hc, p->Hc, s);
-  });
-  if (e != cudaSuccess) return cuda_fail(e, "forward image row pass");
-  e = timed(p, kTimeImgCols, 0.0, s, [&] { return launch_cols_fft(p, p->M, p->d_F, p->Hc, p->Hc, false, nullptr, s); });
-  if (e != cudaSuccess) return cuda_fail(e, "forward image column pass");
-  float* partials = storage == FFST_STORE_F32 ? nullptr : p->d_partials;
-  // F16 stores c_i * s_i with max |c_i s_i| <= 2^15 < 65504; BF16 normalises to <= 1
-  const float target = storage == FFST_STORE_F16 ? 32768.0f : 1.0f;
-  for (const Group& g : p->groups) {
-    const int n = g.p1 - g.p0;
-    e = timed(p, kTimeFwdCols, 0.0, s, [&] { return launch_fwd_cols(p, p->M, g, partials, s); });
-    if (e != cudaSuccess) return cuda_fail(e, "forward column pass");
-    if (partials) {
-      e = timed(p, kTimeOther, 0.0, s, [&] { return launch_plane_scales(p, g, partials, target, plane_scale, s); });
-      if (e != cudaSuccess) return cuda_fail(e, "forward plane scales");
-    }
-    e = timed(p, kTimeFwdRows, (double)n * plane * esz, s, [&] {
-      return launch_rows_c2r(p, p->N, p->d_H, true, 0, 0, g.p0, n,
-                             static_cast<char*>(coeffs) + (long long)g.p0 * plane * esz, storage, plane_scale, plane,
-                             1.0f / (float)plane, s);
-    });
-    if (e != cudaSuccess) return cuda_fail(e, "forward row pass");
-  }
-  return FFST_OK;
+  return analysis(plan, img, coeffs, storage, plane_scale, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" ffst_status ffst_inverse(ffst_plan_t plan, const void* coeffs, int storage, const float* plane_scale,

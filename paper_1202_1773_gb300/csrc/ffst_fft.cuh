@@ -1,17 +1,21 @@
 // Self-written FFT engine: radix-R DFTs in registers and a register-resident
 // Stockham line FFT whose passes exchange data through shared memory.
 //
-// Layout contract of a line FFT of length L run by a team of T threads:
-// thread t of the team holds v[m] = x[t + T*m], m = 0..E-1 (E = L/T), on
-// entry (natural order input) and v[m] = X[t + T*m] on exit (natural order
-// output).  Consecutive threads therefore touch consecutive elements, so the
-// loads before and the stores after the transform are coalesced.
+// Layout contract of a line FFT of length L run by a team of T = L/E
+// threads: thread t holds v[m] = x[t + T*m], m = 0..E-1, on entry (natural
+// order input) and v[m] = X[t + T*m] on exit (natural order output).
+// Consecutive threads therefore touch consecutive elements, so the loads
+// before and the stores after the transform are coalesced.
 //
-// Pass s (radix R, Ns = product of the earlier radices) computes, for every
-// butterfly index j in [0, L/R), the R-point DFT of x[j + r*L/R] after the
-// twiddles W_{Ns R}^{(j mod Ns) r}, and scatters the results to
-// y[(j/Ns) Ns R + (j mod Ns) + r Ns] (the Stockham auto-sort of the FFT
-// literature); the last pass lands exactly in the register layout above.
+// Pass s (radix R = min(E, L/Ns), Ns = product of the earlier radices)
+// computes, for every butterfly index j in [0, L/R), the R-point DFT of
+// x[j + r*L/R] after the twiddles W_{Ns R}^{(j mod Ns) r}, and scatters the
+// results to y[(j/Ns) Ns R + (j mod Ns) + r Ns] (the Stockham auto-sort of
+// the FFT literature); the last pass lands exactly in the register layout.
+//
+// Twiddle table of a (L, E) line: pass s reads W_{Ns R}^{kk r} at index
+// (Ns - 1) + (r - 1) Ns + kk, so consecutive butterflies (consecutive kk)
+// read consecutive addresses; the passes together use L - 1 entries.
 #pragma once
 
 #include <type_traits>
@@ -27,8 +31,6 @@ __device__ __forceinline__ void static_for(F&& f) {
     static_for<I + 1, N>(f);
   }
 }
-
-__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 
 // x * W_R^m with W_R = exp(-2 pi i / R) (forward) or its conjugate (inverse).
 // Multiples of pi/4 are special-cased so no multiply by 0 or 1 is emitted.
@@ -102,33 +104,45 @@ __device__ __forceinline__ void dft(float2 (&x)[R]) {
   }
 }
 
-// Launch geometry of a line FFT of length L (power of two).
-template <int L>
-struct LCfg {
-  static constexpr int E = (L >= 4096) ? 32 : (L >= 16 ? 16 : L);  // elements per thread
-  static constexpr int T = L / E;                                    // threads per line
-  static constexpr int SH = ilog2(E);                                // one pad slot per E elements
-  static constexpr int BUF = L + (L >> SH) + 2;                      // float2 per team buffer
-  __device__ static __forceinline__ int pad(int i) { return i + (i >> SH); }
-};
-
-// Sync policy.  WARP: every team is a run of <= 32 consecutive threads inside
-// one warp, so a warp barrier orders its shared-memory exchange.  Otherwise
-// (teams larger than a warp, or teams interleaved across warps) the whole
-// CTA synchronises, and every thread of the CTA must run the same passes.
-template <bool WARP>
-__device__ __forceinline__ void team_sync() {
-  if constexpr (WARP) __syncwarp();
-  else __syncthreads();
+// Shared-memory slot of element i of a team buffer: one pad slot per E
+// elements keeps the pass-1 scatter (stride E) free of bank conflicts.
+template <int E>
+__device__ __forceinline__ int spad(int i) {
+  return i + (i >> ilog2c(E));
 }
 
-// Stockham passes starting at sub-transform length Ns.  `tw` holds
-// exp(-2 pi i m / L), m = 0..L-1 (FP64-generated, rounded to FP32).
-// With WARP == false every thread of the CTA must call this uniformly.
-template <int L, bool INV, int Ns, bool WARP>
-__device__ __forceinline__ void stockham(float2 (&v)[LCfg<L>::E], float2* buf, int t,
-                                         const float2* __restrict__ tw) {
-  constexpr int E = LCfg<L>::E, T = LCfg<L>::T;
+// float2 slots per team buffer for a line of length L with E per thread,
+// rounded so that (stride mod 16) == skew; consecutive team buffers then
+// start on different banks (skew chosen by the kernel's lane layout).
+__host__ __device__ constexpr int team_stride(int L, int E, int skew) {
+  const int base = L + L / E;
+  return base + ((skew - base % 16) % 16 + 16) % 16;
+}
+
+// Sync policy of a team's shared-memory exchange.
+//  kSyncWarp:  the team is <= 32 consecutive threads inside one warp.
+//  kSyncNamed: the team is a run of whole consecutive warps (NT threads);
+//              it uses hardware barrier `bar` (1..15), other teams do not wait.
+//  kSyncBlock: teams interleaved across warps (or filling the block): the
+//              whole block synchronises and must run the same passes.
+enum { kSyncWarp = 0, kSyncNamed = 1, kSyncBlock = 2 };
+
+template <int SYNC, int NT>
+__device__ __forceinline__ void team_sync(int bar) {
+  if constexpr (SYNC == kSyncWarp) {
+    __syncwarp();
+  } else if constexpr (SYNC == kSyncNamed) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(NT) : "memory");
+  } else {
+    __syncthreads();
+  }
+}
+
+// Stockham passes starting at sub-transform length Ns.  `tw` is the (L, E)
+// pass table (FP64-generated, rounded to FP32), conjugated for INV.
+template <int L, int E, bool INV, int Ns, int SYNC>
+__device__ __forceinline__ void stockham(float2 (&v)[E], float2* buf, int t, const float2* __restrict__ tw, int bar) {
+  constexpr int T = L / E;
   constexpr int REM = L / Ns;
   constexpr int R = REM >= E ? E : REM;
   constexpr int B = E / R;  // butterflies per thread in this pass
@@ -141,10 +155,9 @@ __device__ __forceinline__ void stockham(float2 (&v)[LCfg<L>::E], float2* buf, i
     const int j = t + T * q;
     const int kk = j & (Ns - 1);
     if constexpr (Ns > 1) {
-      constexpr int STRIDE = L / (Ns * R);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2 w = __ldg(&tw[kk * r * STRIDE]);
+        float2 w = __ldg(&tw[(Ns - 1) + (r - 1) * Ns + kk]);
         if (INV) w.y = -w.y;
         x[r] = cmul(x[r], w);
       }
@@ -156,23 +169,24 @@ __device__ __forceinline__ void stockham(float2 (&v)[LCfg<L>::E], float2* buf, i
     } else {
       const int base = (j / Ns) * Ns * R + kk;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[LCfg<L>::pad(base + r * Ns)] = x[r];
+      for (int r = 0; r < R; ++r) buf[spad<E>(base + r * Ns)] = x[r];
     }
   }
   if constexpr (Ns * R < L) {
-    team_sync<WARP>();
+    team_sync<SYNC, T>(bar);
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = buf[LCfg<L>::pad(t + T * m)];
-    team_sync<WARP>();
-    stockham<L, INV, Ns * R, WARP>(v, buf, t, tw);
+    for (int m = 0; m < E; ++m) v[m] = buf[spad<E>(t + T * m)];
+    team_sync<SYNC, T>(bar);
+    stockham<L, E, INV, Ns * R, SYNC>(v, buf, t, tw, bar);
   }
 }
 
 // Full line FFT (unnormalised).  Forward: X[k] = sum x[n] e^{-2 pi i nk/L};
 // inverse: the same with e^{+2 pi i nk/L}.
-template <int L, bool INV, bool WARP>
-__device__ __forceinline__ void line_fft(float2 (&v)[LCfg<L>::E], float2* buf, int t, const float2* __restrict__ tw) {
-  stockham<L, INV, 1, WARP>(v, buf, t, tw);
+template <int L, int E, bool INV, int SYNC>
+__device__ __forceinline__ void line_fft(float2 (&v)[E], float2* buf, int t, const float2* __restrict__ tw,
+                                         int bar = 0) {
+  stockham<L, E, INV, 1, SYNC>(v, buf, t, tw, bar);
 }
 
 }  // namespace ffst

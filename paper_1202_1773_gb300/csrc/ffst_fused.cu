@@ -1,0 +1,79 @@
+// Fused launches for square images: one launch runs the column pass of one
+// plane group interleaved with the row pass of the previous group (forward),
+// or the row pass of one group interleaved with the column pass of the
+// previous one (inverse).  The two halves touch different intermediate
+// buffers, so they are independent; interleaving the blocks lets the
+// HBM-bound row pass and the compute-bound column pass share the SMs.
+#include "ffst_kernels.cuh"
+
+namespace ffst {
+
+template <int M>
+struct FusedCfg {
+  static constexpr size_t SMEM =
+      RowCfg<M / 2>::SMEM > ColCfg<M>::SMEM ? RowCfg<M / 2>::SMEM : ColCfg<M>::SMEM;
+};
+
+template <int M>
+__global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_fwd_fused(FwdColsArgs ca, int nc, C2RArgs ra, int rbx, int nr) {
+  extern __shared__ float2 smem[];
+  int ci = 0, ri = 0;
+  if (split_block(blockIdx.x, nc, nr, &ci, &ri)) fwd_cols_body<M>(ca, ci, smem);
+  else rows_c2r_body<M / 2>(ra, ri % rbx, ri / rbx, smem);
+}
+
+template <int M>
+__global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_inv_fused(R2CArgs ra, int rbx, int nr, InvColsArgs ca, int nc) {
+  extern __shared__ float2 smem[];
+  int ci = 0, ri = 0;
+  if (split_block(blockIdx.x, nc, nr, &ci, &ri)) inv_cols_body<M>(ca, ci, smem);
+  else rows_r2c_body<M / 2>(ra, ri % rbx, ri / rbx, smem);
+}
+
+template <int M>
+static cudaError_t fwd_fused_M(const FwdColsArgs& ca, int nc, const C2RArgs& ra, int nplanes, cudaStream_t s) {
+  const int rbx = (ra.M + RowCfg<M / 2>::TEAMS - 1) / RowCfg<M / 2>::TEAMS;
+  const int nr = rbx * nplanes;
+  if (nc + nr == 0) return cudaSuccess;
+  cudaError_t e = set_smem(k_fwd_fused<M>, FusedCfg<M>::SMEM);
+  if (e != cudaSuccess) return e;
+  k_fwd_fused<M><<<nc + nr, kThreads, FusedCfg<M>::SMEM, s>>>(ca, nc, ra, rbx, nr);
+  return cudaGetLastError();
+}
+
+template <int M>
+static cudaError_t inv_fused_M(const R2CArgs& ra, int nplanes, const InvColsArgs& ca, int nc, cudaStream_t s) {
+  const int rbx = (ra.M + RowCfg<M / 2>::TEAMS - 1) / RowCfg<M / 2>::TEAMS;
+  const int nr = rbx * nplanes;
+  if (nc + nr == 0) return cudaSuccess;
+  cudaError_t e = set_smem(k_inv_fused<M>, FusedCfg<M>::SMEM);
+  if (e != cudaSuccess) return e;
+  k_inv_fused<M><<<nc + nr, kThreads, FusedCfg<M>::SMEM, s>>>(ra, rbx, nr, ca, nc);
+  return cudaGetLastError();
+}
+
+bool fused_supported(int M, int N) { return M == N && M >= 256 && M <= 4096; }
+
+#define FFST_DISPATCH_FUSED(M, CALL)        \
+  switch (M) {                              \
+    case 256: return CALL(256);             \
+    case 512: return CALL(512);             \
+    case 1024: return CALL(1024);           \
+    case 2048: return CALL(2048);           \
+    case 4096: return CALL(4096);           \
+    default: return cudaErrorNotSupported;  \
+  }
+
+cudaError_t launch_fwd_fused(int M, const FwdColsArgs& ca, int nc, const C2RArgs& ra, int nplanes, cudaStream_t s) {
+#define CALL_(MM) fwd_fused_M<MM>(ca, nc, ra, nplanes, s)
+  FFST_DISPATCH_FUSED(M, CALL_)
+#undef CALL_
+}
+
+cudaError_t launch_inv_fused(int M, const R2CArgs& ra, int nplanes, const InvColsArgs& ca, int nc, cudaStream_t s) {
+#define CALL_(MM) inv_fused_M<MM>(ra, nplanes, ca, nc, s)
+  FFST_DISPATCH_FUSED(M, CALL_)
+#undef CALL_
+}
+
+}  // namespace ffst

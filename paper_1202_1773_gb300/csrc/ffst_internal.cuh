@@ -56,6 +56,47 @@ __host__ __device__ constexpr double root_angle(int m, int R) {
 __host__ __device__ constexpr float root_cos(int m, int R) { return (float)taylor_cos(root_angle(m, R)); }
 __host__ __device__ constexpr float root_sin(int m, int R) { return (float)taylor_sin(root_angle(m, R)); }
 
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+// Elements per thread of the line FFTs.  Row kernels transform real rows of
+// length N as complex lines of length L = N/2 (one warp per line at L =
+// 1024); column kernels transform columns of length L = M.
+// Build-time knobs (defaults are the tuned configuration): elements per
+// thread of long row lines, and the minimum resident blocks per SM the
+// compiler must allow for (caps registers per thread at 65536/(256*n)).
+#ifndef FFST_ROW_E_LONG
+#define FFST_ROW_E_LONG 32
+#endif
+#ifndef FFST_MIN_BLOCKS
+#define FFST_MIN_BLOCKS 1
+#endif
+__host__ __device__ constexpr int row_E(int L) { return L >= 1024 ? FFST_ROW_E_LONG : (L >= 16 ? 16 : L); }
+__host__ __device__ constexpr int col_E(int L) { return L >= 4096 ? 32 : (L >= 16 ? 16 : L); }
+
+// Every transform kernel runs 256-thread blocks, so a row-pass block and a
+// column-pass block can share one fused launch.
+constexpr int kThreads = 256;
+
+// Entry idx of the pass twiddle table of a line (L, E) (see ffst_fft.cuh):
+// pass with sub-transform length Ns and radix R = min(E, L/Ns) owns indices
+// [Ns - 1, Ns R - 1); index Ns - 1 + (r - 1) Ns + kk holds W_{Ns R}^{kk r}.
+// Returns the value as the root of unity exp(-2 pi i m / n).
+__host__ __device__ inline void pass_entry(int L, int E, int idx, int* m, int* n) {
+  int Ns = 1;
+  while (Ns < L) {
+    const int R = (L / Ns) < E ? (L / Ns) : E;
+    if (idx < Ns * R - 1) {
+      const int q = idx - (Ns - 1);
+      *m = (q % Ns) * (q / Ns + 1);
+      *n = Ns * R;
+      return;
+    }
+    Ns *= R;
+  }
+  *m = 0;
+  *n = 1;
+}
+
 // ---------------------------------------------------------------------------
 // Plan data shared with the kernels
 // ---------------------------------------------------------------------------
@@ -72,7 +113,7 @@ struct PlaneDesc {
   int W;          // number of support columns (0: plane identically zero)
   int item0;      // first forward column work item of this plane (global index)
   int nitems;     // number of forward column work items
-  int pad_;
+  int rng_off;    // offset of the plane's per-column row ranges (W entries)
   long long off;  // offset of the plane's column-pass intermediate inside its group (float2 units)
 };
 
@@ -102,7 +143,9 @@ enum TimingKind : int {
   kTimeInvCols,       // inverse column FFT, multiply, accumulate
   kTimeOutCols,       // final column IFFT (with normalisation)
   kTimeOutRows,       // final row C2R to the image
-  kTimeOther,         // spectra export, support, clears
+  kTimeFwdFused,      // forward: column pass of group g fused with row pass of group g-1
+  kTimeInvFused,      // inverse: row pass of group g fused with column pass of group g-1
+  kTimeOther,         // spectra export, plane scales
   kTimeKinds
 };
 
@@ -132,12 +175,14 @@ struct ffst_plan_s {
   ffst::PlaneDesc* d_planes = nullptr;
   float* d_tables = nullptr;            // psi1_col | psi1_row | phi_col | phi_row
   ffst::WinParams win{};
-  float2* d_tw_rows = nullptr;          // twiddles of length N (row FFTs)
-  float2* d_tw_cols = nullptr;          // twiddles of length M (column FFTs)
+  float2* d_tw_rows = nullptr;          // pass twiddles of the row lines (N/2, row_E)
+  float2* d_rtw = nullptr;              // exp(-2 pi i k / N), k = 0..N/2 (real-FFT split)
+  float2* d_tw_cols = nullptr;          // pass twiddles of the column lines (M, col_E)
+  int2* d_rng = nullptr;                // per (plane, support column): cyclic row range (start, len)
   float2* d_F = nullptr;                // [M][Hc] image spectrum
   float2* d_S = nullptr;                // [M][Hc] inverse accumulator
-  float* d_D = nullptr;                 // [M][Hc] sum of psi^2
-  float2* d_H = nullptr;                // group intermediate
+  float* d_invD = nullptr;              // [M][Hc] 1 / sum_i psi_i^2 (FP32 psi), inverse normalisation
+  float2* d_H = nullptr;                // two group intermediates (double buffer), h_elems each
   long long h_elems = 0;
   float* d_partials = nullptr;          // [total items] per-panel sums of |psi F| (low-precision storage)
   int total_items = 0;
@@ -157,21 +202,20 @@ ffst_status cuda_fail(cudaError_t e, const char* what);
 void timer_begin(ffst_plan_s* p, int kind, cudaStream_t s, double bytes, cudaEvent_t* out_b);
 void timer_end(ffst_plan_s* p, cudaStream_t s, cudaEvent_t b);
 
-// kernel launchers (ffst_kernels_*.cu); all return cudaGetLastError() of the launch
-cudaError_t launch_rows_r2c(const ffst_plan_s* p, int L, const void* src, int storage, const float* plane_scale,
-                            int plane0, int nplanes, long long src_plane_stride, float2* dst, bool dst_grouped,
-                            int full_c0, int full_W, int dst_ld, cudaStream_t s);
-cudaError_t launch_rows_c2r(const ffst_plan_s* p, int L, const float2* src, bool src_grouped, int full_W, int src_ld,
-                            int plane0, int nplanes, void* dst, int storage, const float* plane_scale,
-                            long long dst_plane_stride, float scale, cudaStream_t s);
-cudaError_t launch_cols_fft(const ffst_plan_s* p, int L, float2* buf, int width, int ld, bool inverse,
-                            const float* divisor, cudaStream_t s);
-cudaError_t launch_inv_cols(const ffst_plan_s* p, int L, const Group& g, bool first, cudaStream_t s);
+// plan-time kernels (ffst_plan.cu)
 cudaError_t launch_spectra(const ffst_plan_s* p, float* psi, cudaStream_t s);
 cudaError_t launch_support(const ffst_plan_s* p, int* d_minmax, cudaStream_t s);
-cudaError_t launch_fwd_cols(const ffst_plan_s* p, int L, const Group& g, float* partials, cudaStream_t s);
+cudaError_t launch_ranges(const ffst_plan_s* p, cudaStream_t s);
+cudaError_t launch_inv_norm(const ffst_plan_s* p, cudaStream_t s);
 cudaError_t launch_plane_scales(const ffst_plan_s* p, const Group& g, const float* partials, float target,
                                 float* plane_scale, cudaStream_t s);
+
+// Opt a kernel into more than 48 KB of dynamic shared memory (once per kernel).
+template <typename K>
+inline cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 // per-length launch geometry of the column kernels (columns per CTA)
 int cols_per_cta(int L);

@@ -1,0 +1,380 @@
+// Device bodies of the transform kernels.  Each body works on one logical
+// block (given explicitly), so the same code runs in a standalone kernel or
+// inside a fused launch that interleaves row-pass and column-pass blocks.
+// All bodies assume kThreads (256) threads per block.
+//
+// Row passes (real rows of length N <-> half spectra, columns 0..N/2): a real
+// row x is transformed as the complex line z[n] = x[2n] + i x[2n+1] of
+// length L = N/2 (the real-input FFT of the signal-processing literature):
+//  R2C: Z = FFT_L(z);  X[k] = E[k] + W_N^k O[k] with
+//       E[k] = (Z[k] + conj Z[L-k]) / 2,  O[k] = (Z[k] - conj Z[L-k]) / (2i),
+//       for the kept columns k in [c0, c0 + W) of [0, N/2] (W_N = e^{-2 pi i/N}).
+//  C2R: Z[k] = (X[k] + conj X[L-k]) + i W_N^{-k} (X[k] - conj X[L-k]),
+//       k in [0, L); z = IFFT_L(Z) holds x[2n] + i x[2n+1] (times N for the
+//       unnormalised inverse).  Columns outside [c0, c0 + W) are zero (the
+//       plane's spectral support); the imaginary parts of X[0] and X[N/2]
+//       are dropped (Hermitian part).
+//
+// Column passes (half-spectrum buffers [M][ld], complex, row-major): a block
+// owns a panel of P adjacent columns; thread (t, c) is threadIdx.x = t*P + c,
+// so the P columns of one row are read or written by consecutive lanes.
+// Each column is transformed by the T threads with the same c; their
+// shared-memory exchanges use block barriers.  Within a plane's support
+// column, psi_hat is nonzero only on one cyclic row interval (start, len)
+// computed at plan time; the window is generated and F is read only there.
+#pragma once
+
+#include "ffst_fft.cuh"
+#include "ffst_window.cuh"
+
+namespace ffst {
+
+// ---------------------------------------------------------------------------
+// storage of a coefficient stack (runtime code, uniform over a launch)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int stor_bytes(int st) { return st == FFST_STORE_F32 ? 4 : 2; }
+
+__device__ __forceinline__ float2 load_pair(const void* p, long long i, int st) {  // elements i, i+1 (i even)
+  if (st == FFST_STORE_F32)
+    return __ldg(reinterpret_cast<const float2*>(static_cast<const float*>(p) + i));
+  if (st == FFST_STORE_F16)
+    return __half22float2(*reinterpret_cast<const __half2*>(static_cast<const __half*>(p) + i));
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(static_cast<const __nv_bfloat16*>(p) + i));
+}
+
+__device__ __forceinline__ void store_pair(void* p, long long i, float a, float b, int st) {
+  if (st == FFST_STORE_F32)
+    *reinterpret_cast<float2*>(static_cast<float*>(p) + i) = make_float2(a, b);
+  else if (st == FFST_STORE_F16)
+    *reinterpret_cast<__half2*>(static_cast<__half*>(p) + i) = __floats2half2_rn(a, b);
+  else
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(p) + i) = __floats2bfloat162_rn(a, b);
+}
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+template <int L>
+struct RowCfg {
+  static constexpr int E = row_E(L);
+  static constexpr int T = L / E;
+  static constexpr int TEAMS = (T >= kThreads) ? 1 : kThreads / T;  // rows per block
+  static constexpr int SYNC = T <= 32 ? kSyncWarp : (T < kThreads ? kSyncNamed : kSyncBlock);
+  static constexpr int BUF = team_stride(L, E, T < 16 ? T : 0);
+  static constexpr size_t SMEM = sizeof(float2) * TEAMS * BUF;
+  static_assert(TEAMS * T == kThreads, "row teams must fill the block");
+};
+
+template <int L>
+struct ColCfg {
+  static constexpr int E = col_E(L);
+  static constexpr int T = L / E;
+  static constexpr int P = kThreads / T;  // columns per block
+  static constexpr int BUF = team_stride(L, E, P >= 16 ? 1 : 16 / P);
+  static constexpr size_t SMEM = sizeof(float2) * P * BUF;
+  static_assert(P * T == kThreads, "column teams must fill the block");
+};
+
+__device__ __forceinline__ bool in_range(int row, int2 rg, int M) { return ((row - rg.x) & (M - 1)) < rg.y; }
+
+// ---------------------------------------------------------------------------
+// row passes
+// ---------------------------------------------------------------------------
+struct R2CArgs {
+  const void* src;           // plane 0 of the batch (row-major rows x 2L)
+  long long src_plane_stride;
+  int st;                    // storage code of src
+  const float* plane_scale;  // per plane s_i (low-precision storage) or null
+  int plane0;                // plane index of by == 0 (for descriptors/scales)
+  int M;                     // rows
+  float2* dst;               // grouped: base of the group's intermediate
+  const PlaneDesc* planes;   // non-null: grouped output (per-plane c0, W, off)
+  int c0, W, ld;             // used when planes == null
+  const float2* tw;          // pass table (L, E)
+  const float2* rtw;         // W_N^k, k = 0..L
+};
+
+template <int L>
+__device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, float2* smem) {
+  constexpr int E = RowCfg<L>::E, T = RowCfg<L>::T, N = 2 * L;
+  const int team = threadIdx.x / T, t = threadIdx.x % T;
+  float2* buf = smem + team * RowCfg<L>::BUF;
+  const int plane = a.plane0 + by;
+  const int row = bx * RowCfg<L>::TEAMS + team;
+  const bool act = row < a.M;
+  const void* src = static_cast<const char*>(a.src) + (long long)by * a.src_plane_stride * stor_bytes(a.st);
+  const float us = (a.st != FFST_STORE_F32 && a.plane_scale) ? 1.0f / __ldg(&a.plane_scale[plane]) : 1.0f;
+  float2 v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const float2 x = act ? load_pair(src, (long long)row * N + 2 * (t + T * m), a.st) : make_float2(0.f, 0.f);
+    v[m] = make_float2(x.x * us, x.y * us);
+  }
+  line_fft<L, E, false, RowCfg<L>::SYNC>(v, buf, t, a.tw, 1 + team);
+#pragma unroll
+  for (int m = 0; m < E; ++m) buf[spad<E>(t + T * m)] = v[m];
+  team_sync<RowCfg<L>::SYNC, T>(1 + team);
+  if (!act) return;
+  int c0 = a.c0, W = a.W, ld = a.ld;
+  float2* dst = a.dst;
+  if (a.planes) {
+    const PlaneDesc d = a.planes[plane];
+    c0 = d.c0;
+    W = d.W;
+    ld = d.W;
+    dst = a.dst + d.off;
+  }
+  float2* drow = dst + (long long)row * ld;
+  for (int idx = t; idx < W; idx += T) {
+    const int k = c0 + idx;  // 0 .. L
+    const float2 zk = buf[spad<E>(k & (L - 1))];
+    const float2 zn = buf[spad<E>((L - k) & (L - 1))];
+    const float2 e = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+    const float2 o = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
+    const float2 w = __ldg(&a.rtw[k]);
+    drow[idx] = make_float2(e.x + w.x * o.x - w.y * o.y, e.y + w.x * o.y + w.y * o.x);
+  }
+}
+
+struct C2RArgs {
+  const float2* src;        // grouped: base of the group's intermediate
+  const PlaneDesc* planes;  // non-null: grouped input (per-plane c0, W, off)
+  int c0, W, ld;            // used when planes == null
+  int M;
+  int plane0;
+  void* dst;                // plane 0 of the batch
+  long long dst_plane_stride;
+  int st;                   // storage code of dst
+  const float* plane_scale;  // low-precision storage: multiply by s_i before rounding
+  float scale;               // 1/(M N)
+  const float2* tw;
+  const float2* rtw;
+};
+
+template <int L>
+__device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, float2* smem) {
+  constexpr int E = RowCfg<L>::E, T = RowCfg<L>::T, N = 2 * L;
+  const int team = threadIdx.x / T, t = threadIdx.x % T;
+  float2* buf = smem + team * RowCfg<L>::BUF;
+  const int plane = a.plane0 + by;
+  const int row = bx * RowCfg<L>::TEAMS + team;
+  const bool act = row < a.M;
+  int c0 = a.c0, W = a.W, ld = a.ld;
+  const float2* src = a.src;
+  if (a.planes) {
+    const PlaneDesc d = a.planes[plane];
+    c0 = d.c0;
+    W = d.W;
+    ld = d.W;
+    src = a.src + d.off;
+  }
+  const float2* srow = src + (long long)row * ld;
+  float s = a.scale;
+  if (a.st != FFST_STORE_F32 && a.plane_scale) s *= __ldg(&a.plane_scale[plane]);
+  float2 v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = t + T * m;
+    const int ia = k - c0, ib = L - k - c0;
+    float2 xa = (act && (unsigned)ia < (unsigned)W) ? srow[ia] : make_float2(0.f, 0.f);
+    float2 xb = (act && (unsigned)ib < (unsigned)W) ? srow[ib] : make_float2(0.f, 0.f);
+    if (k == 0) {  // X[0] and X[N/2]: Hermitian part is real
+      xa.y = 0.f;
+      xb.y = 0.f;
+    }
+    const float2 e = make_float2(xa.x + xb.x, xa.y - xb.y);  // X[k] + conj X[L-k]
+    const float2 d = make_float2(xa.x - xb.x, xa.y + xb.y);  // X[k] - conj X[L-k]
+    float2 w = __ldg(&a.rtw[k]);                             // W_N^k; W_N^{-k} = conj
+    w.x *= s;
+    w.y *= s;
+    const float2 wd = make_float2(w.x * d.x + w.y * d.y, w.x * d.y - w.y * d.x);
+    v[m] = make_float2(fmaf(e.x, s, -wd.y), fmaf(e.y, s, wd.x));
+  }
+  line_fft<L, E, true, RowCfg<L>::SYNC>(v, buf, t, a.tw, 1 + team);
+  if (!act) return;
+  void* dst = static_cast<char*>(a.dst) + (long long)by * a.dst_plane_stride * stor_bytes(a.st);
+#pragma unroll
+  for (int m = 0; m < E; ++m) store_pair(dst, (long long)row * N + 2 * (t + T * m), v[m].x, v[m].y, a.st);
+}
+
+// ---------------------------------------------------------------------------
+// column passes
+// ---------------------------------------------------------------------------
+
+// In-place column FFTs of columns [0, width) of buf (row stride ld).  When
+// `scale_tab` is given (same layout), each element is multiplied by it first.
+template <int L, bool INV>
+__device__ __forceinline__ void cols_fft_body(float2* __restrict__ buf, int width, int ld,
+                                              const float* __restrict__ scale_tab, const float2* __restrict__ tw,
+                                              int bx, float2* smem) {
+  constexpr int E = ColCfg<L>::E, T = ColCfg<L>::T, P = ColCfg<L>::P;
+  const int t = threadIdx.x / P, cl = threadIdx.x % P;
+  const int c = bx * P + cl;
+  const bool act = c < width;
+  float2 v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const long long at = (long long)(t + T * m) * ld + c;
+    float2 x = act ? buf[at] : make_float2(0.f, 0.f);
+    if (scale_tab && act) x = cscale(x, __ldg(&scale_tab[at]));
+    v[m] = x;
+  }
+  line_fft<L, E, INV, kSyncBlock>(v, smem + cl * ColCfg<L>::BUF, t, tw);
+  if (act) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) buf[(long long)(t + T * m) * ld + c] = v[m];
+  }
+}
+
+struct FwdColsArgs {
+  const float2* F;          // image half spectrum [M][Hc]
+  int Hc;
+  const PlaneDesc* planes;
+  const ColItem* items;     // items of this group (index 0 = first item of the group)
+  const int2* rng;
+  float2* H;                // base of the group's intermediate
+  WinParams w;
+  const float2* tw;
+  float* partials;          // per item sum |G| (low-precision storage), or null
+};
+
+// Forward column pass of one plane panel (Sec. 3.1 eq. shearletTransform):
+// G = psi_hat_i * F on the panel's columns, then the column IFFT; the result
+// goes to the plane's slot of the group intermediate, [M][W_i] starting at
+// column c0_i.  The team of a column evaluates psi only on the column's
+// support rows (one cyclic interval, consecutive rows on consecutive
+// threads), reads F only there, and passes G through its shared buffer into
+// the register layout of the FFT.  With `partials` the block also writes
+// sum |G| over its panel, each column counted once for itself and once for
+// its conjugate partner (columns 0 and N/2 are their own partners); a
+// plane's partials add up to sum_omega |G(omega)| >= M N max_m |c_i(m)|.
+template <int L>
+__device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int item, float2* smem) {
+  constexpr int E = ColCfg<L>::E, T = ColCfg<L>::T, P = ColCfg<L>::P;
+  __shared__ float red[kThreads / 32];
+  const int t = threadIdx.x / P, cl = threadIdx.x % P;
+  float2* buf = smem + cl * ColCfg<L>::BUF;
+  const ColItem it = a.items[item];
+  const PlaneDesc d = a.planes[it.plane];
+  const int c = it.col + cl;
+  const bool act = c < d.c0 + d.W;
+  const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
+  float mag = 0.0f;
+  for (int q = t; q < rg.y; q += T) {
+    const int row = (rg.x + q) & (L - 1);
+    const float psi = win_at(a.w, d, row, c);
+    float2 g = make_float2(0.f, 0.f);
+    if (psi != 0.0f) g = cscale(a.F[(long long)row * a.Hc + c], psi);
+    buf[spad<E>(row)] = g;
+    if (a.partials) mag += sqrtf(g.x * g.x + g.y * g.y);
+  }
+  __syncthreads();
+  float2 v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int row = t + T * m;
+    v[m] = in_range(row, rg, L) ? buf[spad<E>(row)] : make_float2(0.f, 0.f);
+  }
+  if (a.partials) {
+    const bool self_partner = (c == 0) || (2 * c == a.w.N);
+    mag *= self_partner ? 1.0f : 2.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mag += __shfl_xor_sync(0xffffffffu, mag, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mag;
+  }
+  __syncthreads();  // buf reads done (and red written) before the FFT reuses buf
+  if (a.partials && threadIdx.x == 0) {
+    float sum = 0.0f;
+    for (int q = 0; q < kThreads / 32; ++q) sum += red[q];
+    a.partials[item] = sum;
+  }
+  line_fft<L, E, true, kSyncBlock>(v, buf, t, a.tw);
+  if (act) {
+    float2* out = a.H + d.off + (c - d.c0);
+#pragma unroll
+    for (int m = 0; m < E; ++m) out[(long long)(t + T * m) * d.W] = v[m];
+  }
+}
+
+struct InvColsArgs {
+  const float2* H;          // base of the group's intermediate
+  int Hc;
+  const PlaneDesc* planes;
+  int p0, p1;               // planes of the group
+  const int2* rng;
+  float2* S;                // [M][Hc] accumulator (zeroed before the first group)
+  WinParams w;
+  const float2* tw;
+};
+
+// Inverse column pass (Sec. 3.3 eq. inverseShearletTransform): for every plane
+// of the group whose support meets this block's panel, column FFT of the
+// plane's row spectra, then S += psi_hat_i * (that) on the column's support
+// rows (one cyclic interval, walked by consecutive threads through the
+// team's shared buffer).  Each block owns its columns and visits planes in
+// index order, so the sums are deterministic.
+template <int L>
+__device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, float2* smem) {
+  constexpr int E = ColCfg<L>::E, T = ColCfg<L>::T, P = ColCfg<L>::P;
+  const int t = threadIdx.x / P, cl = threadIdx.x % P;
+  float2* buf = smem + cl * ColCfg<L>::BUF;
+  const int cbase = bx * P;
+  const int c = cbase + cl;
+  for (int p = a.p0; p < a.p1; ++p) {
+    const PlaneDesc d = a.planes[p];
+    if (d.W == 0 || d.c0 >= cbase + P || d.c0 + d.W <= cbase) continue;  // uniform over the block
+    const bool act = c >= d.c0 && c < d.c0 + d.W;
+    const float2* in = a.H + d.off + (c - d.c0);
+    float2 v[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = act ? in[(long long)(t + T * m) * d.W] : make_float2(0.f, 0.f);
+    const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
+    line_fft<L, E, false, kSyncBlock>(v, buf, t, a.tw);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int row = t + T * m;
+      if (in_range(row, rg, L)) buf[spad<E>(row)] = v[m];
+    }
+    __syncthreads();
+    for (int q = t; q < rg.y; q += T) {
+      const int row = (rg.x + q) & (L - 1);
+      const float psi = win_at(a.w, d, row, c);
+      const float2 x = buf[spad<E>(row)];
+      float2* sp = a.S + (long long)row * a.Hc + c;
+      const float2 old = *sp;
+      *sp = make_float2(fmaf(psi, x.x, old.x), fmaf(psi, x.y, old.y));
+    }
+    __syncthreads();  // buf reads done before the next plane's FFT
+  }
+}
+
+// Block b of a launch that interleaves nc column blocks among nr row blocks
+// in proportion: returns true for a column block with index *ci, false for a
+// row block with index *ri.  Every index in [0, nc) and [0, nr) occurs once.
+__device__ __forceinline__ bool split_block(int b, int nc, int nr, int* ci, int* ri) {
+  const long long total = (long long)nc + nr;
+  const int lo = (int)((long long)b * nc / total), hi = (int)((long long)(b + 1) * nc / total);
+  if (hi > lo) {
+    *ci = lo;
+    return true;
+  }
+  *ri = b - lo;
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// launchers (ffst_rows.cu, ffst_cols.cu, ffst_fused.cu)
+// ---------------------------------------------------------------------------
+cudaError_t launch_rows_r2c(int L, const R2CArgs& a, int nplanes, cudaStream_t s);
+cudaError_t launch_rows_c2r(int L, const C2RArgs& a, int nplanes, cudaStream_t s);
+cudaError_t launch_cols_fft(int L, float2* buf, int width, int ld, bool inverse, const float* scale_tab,
+                            const float2* tw, cudaStream_t s);
+cudaError_t launch_fwd_cols(int L, const FwdColsArgs& a, int nitems, cudaStream_t s);
+cudaError_t launch_inv_cols(int L, const InvColsArgs& a, int npanels, cudaStream_t s);
+// Fused launches exist for square images with 256 <= M <= 4096 (fused_supported);
+// other sizes return cudaErrorNotSupported and use the standalone kernels.
+bool fused_supported(int M, int N);
+cudaError_t launch_fwd_fused(int M, const FwdColsArgs& ca, int nc, const C2RArgs& ra, int nplanes, cudaStream_t s);
+cudaError_t launch_inv_fused(int M, const R2CArgs& ra, int nplanes, const InvColsArgs& ca, int nc, cudaStream_t s);
+
+}  // namespace ffst

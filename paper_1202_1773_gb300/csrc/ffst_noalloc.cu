@@ -27,9 +27,10 @@
 // before anything is enqueued.  Spectral supports are not pruned here (every
 // column of every plane is transformed); results equal ffst_forward's to
 // FP32 rounding.
+#include <cstring>
 #include <mutex>
 
-#include "ffst_window.cuh"
+#include "ffst_kernels.cuh"
 
 namespace ffst {
 namespace {
@@ -49,9 +50,11 @@ constexpr long long kOffH = align256(kOffF + kNaSpec * 8);
 constexpr long long kOffPlanes = align256(kOffH + kNaGroup * kNaSpec * 8);
 constexpr long long kOffItems = align256(kOffPlanes + kNaMaxPlanes * (long long)sizeof(PlaneDesc));
 constexpr long long kOffTab = align256(kOffItems + kNaMaxItems * (long long)sizeof(ColItem));
-constexpr long long kOffTwR = align256(kOffTab + kNaTabFloats * 4);
-constexpr long long kOffTwC = align256(kOffTwR + kNaMaxSide * 8);
-constexpr long long kNoallocBytes = align256(kOffTwC + kNaMaxSide * 8);
+constexpr long long kOffTwR = align256(kOffTab + kNaTabFloats * 4);            // row pass table, N/2 entries
+constexpr long long kOffRtw = align256(kOffTwR + (kNaMaxSide / 2) * 8);          // real split, N/2 + 1 entries
+constexpr long long kOffTwC = align256(kOffRtw + (kNaMaxSide / 2 + 1) * 8);      // column pass table, M entries
+constexpr long long kOffRng = align256(kOffTwC + kNaMaxSide * 8);                // row ranges, eta x (N/2 + 1)
+constexpr long long kNoallocBytes = align256(kOffRng + kNaMaxPlanes * (kNaMaxSide / 2 + 1) * 8LL);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
@@ -82,11 +85,19 @@ __device__ double na_varphi(double w) {
 struct NaSetup {
   int M, N, j0, eta, Hc, P, ipp;  // ipp: column panels per plane
   float* tab;                      // psi1_col | psi1_row | phi_col | phi_row
-  float2* twr;                     // e^{-2 pi i m/N}
-  float2* twc;                     // e^{-2 pi i m/M}
+  float2* twr;                     // pass table of the row lines (N/2, row_E)
+  float2* rtw;                     // e^{-2 pi i k/N}, k = 0..N/2
+  float2* twc;                     // pass table of the column lines (M, col_E)
+  int2* rng;                       // row ranges: the full column for every (plane, column)
   PlaneDesc* planes;
   ColItem* items;
 };
+
+__device__ float2 na_root(int m, int n) {
+  double sn, cs;
+  sincospi(2.0 * m / n, &sn, &cs);
+  return make_float2((float)cs, (float)-sn);
+}
 
 // Plane index -> (kappa, j, k) in the order of Sec. 3.5.2.
 __device__ void na_plane(int i, int* kappa, int* j, int* k) {
@@ -131,16 +142,19 @@ __global__ void k_na_setup(NaSetup s) {
   }
   for (int q = tid; q <= hn; q += stride) phi_col[q] = (float)na_varphi(q * dc);
   for (int q = tid; q <= hm; q += stride) phi_row[q] = (float)na_varphi(q * dr);
-  for (int q = tid; q < s.N; q += stride) {
-    double sn, cs;
-    sincospi(2.0 * q / s.N, &sn, &cs);
-    s.twr[q] = make_float2((float)cs, (float)-sn);
+  const int Lr = s.N / 2;
+  for (int q = tid; q < Lr; q += stride) {
+    int m = 0, n = 1;
+    if (q < Lr - 1) pass_entry(Lr, row_E(Lr), q, &m, &n);
+    s.twr[q] = na_root(m, n);
   }
+  for (int q = tid; q <= Lr; q += stride) s.rtw[q] = na_root(q, s.N);
   for (int q = tid; q < s.M; q += stride) {
-    double sn, cs;
-    sincospi(2.0 * q / s.M, &sn, &cs);
-    s.twc[q] = make_float2((float)cs, (float)-sn);
+    int m = 0, n = 1;
+    if (q < s.M - 1) pass_entry(s.M, col_E(s.M), q, &m, &n);
+    s.twc[q] = na_root(m, n);
   }
+  for (int q = tid; q < s.eta * s.Hc; q += stride) s.rng[q] = make_int2(0, s.M);
   for (int i = tid; i < s.eta; i += stride) {
     PlaneDesc d{};
     na_plane(i, &d.kappa, &d.j, &d.k);
@@ -148,6 +162,7 @@ __global__ void k_na_setup(NaSetup s) {
     d.W = s.Hc;
     d.item0 = i * s.ipp;
     d.nitems = s.ipp;
+    d.rng_off = i * s.Hc;
     d.off = (long long)(i % kNaGroup) * s.M * s.Hc;
     s.planes[i] = d;
   }
@@ -214,7 +229,9 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
   P.d_planes = reinterpret_cast<PlaneDesc*>(base + kOffPlanes);
   P.d_items = reinterpret_cast<ColItem*>(base + kOffItems);
   P.d_tw_rows = reinterpret_cast<float2*>(base + kOffTwR);
+  P.d_rtw = reinterpret_cast<float2*>(base + kOffRtw);
   P.d_tw_cols = reinterpret_cast<float2*>(base + kOffTwC);
+  P.d_rng = reinterpret_cast<int2*>(base + kOffRng);
   float* tab = reinterpret_cast<float*>(base + kOffTab);
   P.win.M = rows;
   P.win.N = cols;
@@ -235,7 +252,9 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
   su.ipp = (P.Hc + su.P - 1) / su.P;
   su.tab = tab;
   su.twr = P.d_tw_rows;
+  su.rtw = P.d_rtw;
   su.twc = P.d_tw_cols;
+  su.rng = P.d_rng;
   su.planes = P.d_planes;
   su.items = P.d_items;
   k_na_setup<<<64, 256, 0, s>>>(su);
@@ -243,15 +262,45 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
   if (e != cudaSuccess) return cuda_fail(e, "ffst_forward_noalloc: setup");
 
   const long long plane = (long long)rows * cols;
-  e = launch_rows_r2c(&P, cols, img, FFST_STORE_F32, nullptr, 0, 1, 0, P.d_F, false, 0, P.Hc, P.Hc, s);
-  if (e == cudaSuccess) e = launch_cols_fft(&P, rows, P.d_F, P.Hc, P.Hc, false, nullptr, s);
+  R2CArgs ia;
+  std::memset(&ia, 0, sizeof(ia));
+  ia.src = img;
+  ia.st = FFST_STORE_F32;
+  ia.M = rows;
+  ia.dst = P.d_F;
+  ia.W = P.Hc;
+  ia.ld = P.Hc;
+  ia.tw = P.d_tw_rows;
+  ia.rtw = P.d_rtw;
+  e = launch_rows_r2c(cols / 2, ia, 1, s);
+  if (e == cudaSuccess) e = launch_cols_fft(rows, P.d_F, P.Hc, P.Hc, false, nullptr, P.d_tw_cols, s);
   for (int p0 = 0; p0 < P.eta && e == cudaSuccess; p0 += kNaGroup) {
     const int p1 = p0 + kNaGroup < P.eta ? p0 + kNaGroup : P.eta;
-    Group g{p0, p1, (long long)(p1 - p0) * rows * P.Hc, p0 * su.ipp, (p1 - p0) * su.ipp};
-    e = launch_fwd_cols(&P, rows, g, nullptr, s);
-    if (e == cudaSuccess)
-      e = launch_rows_c2r(&P, cols, P.d_H, true, 0, 0, p0, p1 - p0, coeffs + (long long)p0 * plane, FFST_STORE_F32,
-                          nullptr, plane, 1.0f / (float)plane, s);
+    FwdColsArgs ca;
+    ca.F = P.d_F;
+    ca.Hc = P.Hc;
+    ca.planes = P.d_planes;
+    ca.items = P.d_items + p0 * su.ipp;
+    ca.rng = P.d_rng;
+    ca.H = P.d_H;
+    ca.w = P.win;
+    ca.tw = P.d_tw_cols;
+    ca.partials = nullptr;
+    e = launch_fwd_cols(rows, ca, (p1 - p0) * su.ipp, s);
+    if (e != cudaSuccess) break;
+    C2RArgs ra;
+    std::memset(&ra, 0, sizeof(ra));
+    ra.src = P.d_H;
+    ra.planes = P.d_planes;
+    ra.M = rows;
+    ra.plane0 = p0;
+    ra.dst = coeffs + (long long)p0 * plane;
+    ra.dst_plane_stride = plane;
+    ra.st = FFST_STORE_F32;
+    ra.scale = 1.0f / (float)plane;
+    ra.tw = P.d_tw_rows;
+    ra.rtw = P.d_rtw;
+    e = launch_rows_c2r(cols / 2, ra, p1 - p0, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "ffst_forward_noalloc: transform");
   return FFST_OK;

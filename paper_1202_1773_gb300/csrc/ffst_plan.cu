@@ -7,7 +7,7 @@
 #include <cstring>
 #include <memory>
 
-#include "ffst_window.cuh"
+#include "ffst_kernels.cuh"
 
 namespace ffst {
 
@@ -93,6 +93,77 @@ cudaError_t launch_support(const ffst_plan_s* p, int* d_minmax, cudaStream_t s) 
   return cudaGetLastError();
 }
 
+// For every plane and support column, the shortest cyclic row interval
+// (start, len) that holds all nonzero rows: the complement of the largest
+// cyclic gap between consecutive nonzero rows.  One CTA per plane.
+__global__ void k_ranges(WinParams w, const PlaneDesc* __restrict__ planes, int2* __restrict__ rng) {
+  const PlaneDesc d = planes[blockIdx.x];
+  for (int q = threadIdx.x; q < d.W; q += blockDim.x) {
+    const int c = d.c0 + q;
+    int first = -1, prev = -1, maxgap = -1, after = 0;
+    for (int r = 0; r < w.M; ++r) {
+      if (win_at(w, d, r, c) != 0.0f) {
+        if (first < 0) {
+          first = r;
+        } else {
+          const int gap = r - prev - 1;
+          if (gap > maxgap) {
+            maxgap = gap;
+            after = r;
+          }
+        }
+        prev = r;
+      }
+    }
+    int2 out = make_int2(0, 0);
+    if (first >= 0) {
+      const int wrap = first + w.M - prev - 1;
+      out = (wrap >= maxgap) ? make_int2(first, prev - first + 1) : make_int2(after, w.M - maxgap);
+    }
+    rng[d.rng_off + q] = out;
+  }
+}
+
+// 1 / sum_i psi_i^2 on the half spectrum, from the same FP32 generator the
+// transforms use (the inverse's normalisation, Sec. 3.3).
+__global__ void k_inv_norm(WinParams w, const PlaneDesc* __restrict__ planes, int eta, int Hc,
+                           const int2* __restrict__ rng, float* __restrict__ inv_d) {
+  extern __shared__ PlaneDesc sp[];
+  for (int i = threadIdx.x; i < eta; i += blockDim.x) sp[i] = planes[i];
+  __syncthreads();
+  const long long total = (long long)w.M * Hc;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int pr = (int)(idx / Hc), pc = (int)(idx % Hc);
+    float sum = 0.0f;
+    for (int i = 0; i < eta; ++i) {
+      const PlaneDesc& d = sp[i];
+      const int q = pc - d.c0;
+      if (q < 0 || q >= d.W) continue;
+      const int2 rg = rng[d.rng_off + q];
+      if (((pr - rg.x) & (w.M - 1)) >= rg.y) continue;
+      const float psi = win_at(w, d, pr, pc);
+      sum = fmaf(psi, psi, sum);
+    }
+    inv_d[idx] = sum > 0.0f ? 1.0f / sum : 1.0f;
+  }
+}
+
+cudaError_t launch_ranges(const ffst_plan_s* p, cudaStream_t s) {
+  k_ranges<<<p->eta, 256, 0, s>>>(p->win, p->d_planes, p->d_rng);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inv_norm(const ffst_plan_s* p, cudaStream_t s) {
+  const size_t smem = sizeof(PlaneDesc) * p->eta;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_inv_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_inv_norm<<<152 * 8, 256, smem, s>>>(p->win, p->d_planes, p->eta, p->Hc, p->d_rng, p->d_invD);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // error handling
 // ---------------------------------------------------------------------------
@@ -117,10 +188,12 @@ static void free_plan(ffst_plan_s* p) {
   cudaFree(p->d_planes);
   cudaFree(p->d_tables);
   cudaFree(p->d_tw_rows);
-  if (p->d_tw_cols != p->d_tw_rows) cudaFree(p->d_tw_cols);
+  cudaFree(p->d_tw_cols);
+  cudaFree(p->d_rtw);
+  cudaFree(p->d_rng);
   cudaFree(p->d_F);
   cudaFree(p->d_S);
-  cudaFree(p->d_D);
+  cudaFree(p->d_invD);
   cudaFree(p->d_H);
   cudaFree(p->d_partials);
   cudaFree(p->d_items);
@@ -133,10 +206,10 @@ static void free_plan(ffst_plan_s* p) {
 }
 
 // Intermediate budget per plane group.  The column pass writes a group's
-// intermediates and the row pass reads them back; keeping a group within
-// a fraction of the 126 MB L2 lets that round trip stay on chip.
+// intermediates and the row pass reads them back; two groups are in flight
+// (double buffer), so 2 x 32 MB plus F and S stay within the 126 MB L2.
 static long long group_budget_elems() {
-  double mb = 48.0;
+  double mb = 32.0;
   if (const char* e = std::getenv("FFST_GROUP_MB")) {
     const double v = std::atof(e);
     if (v > 0.0) mb = v;
@@ -144,13 +217,32 @@ static long long group_budget_elems() {
   return (long long)(mb * 1024.0 * 1024.0 / sizeof(float2));
 }
 
-static std::vector<float2> twiddles(int L) {
-  std::vector<float2> t(L);
-  for (int m = 0; m < L; ++m) {
-    const double a = 2.0 * kPi * (double)m / (double)L;
-    t[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+// Pass twiddle table of a line (L, E) (layout in ffst_fft.cuh), FP64 -> FP32.
+static std::vector<float2> pass_table(int L, int E) {
+  std::vector<float2> t(L > 1 ? L : 1, make_float2(1.0f, 0.0f));
+  for (int idx = 0; idx < L - 1; ++idx) {
+    int m = 0, n = 1;
+    pass_entry(L, E, idx, &m, &n);
+    const double a = 2.0 * kPi * (double)m / (double)n;
+    t[idx] = make_float2((float)std::cos(a), (float)-std::sin(a));
   }
   return t;
+}
+
+// exp(-2 pi i k / N), k = 0..N/2: the split twiddles of the real-row FFTs.
+static std::vector<float2> real_twiddles(int N) {
+  std::vector<float2> t(N / 2 + 1);
+  for (int k = 0; k <= N / 2; ++k) {
+    const double a = 2.0 * kPi * (double)k / (double)N;
+    t[k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  return t;
+}
+
+static cudaError_t upload(float2** dst, const std::vector<float2>& v) {
+  cudaError_t e = cudaMalloc(dst, v.size() * sizeof(float2));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, v.data(), v.size() * sizeof(float2), cudaMemcpyHostToDevice);
 }
 
 }  // namespace ffst
@@ -231,19 +323,10 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
   p->win.phi_col = p->win.psi1_row + (size_t)j0 * nrow;
   p->win.phi_row = p->win.phi_col + ncol;
 
-  // twiddles (FP64 -> FP32)
-  {
-    auto tr = twiddles(cols);
-    if ((e = cudaMalloc(&p->d_tw_rows, tr.size() * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "twiddles");
-    cudaMemcpy(p->d_tw_rows, tr.data(), tr.size() * sizeof(float2), cudaMemcpyHostToDevice);
-    if (rows == cols) {
-      p->d_tw_cols = p->d_tw_rows;
-    } else {
-      auto tc = twiddles(rows);
-      if ((e = cudaMalloc(&p->d_tw_cols, tc.size() * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "twiddles");
-      cudaMemcpy(p->d_tw_cols, tc.data(), tc.size() * sizeof(float2), cudaMemcpyHostToDevice);
-    }
-  }
+  // twiddles (FP64 -> FP32): row lines of length N/2, their real split, column lines of length M
+  if ((e = upload(&p->d_tw_rows, pass_table(cols / 2, row_E(cols / 2)))) != cudaSuccess) return cuda_fail(e, "twiddles");
+  if ((e = upload(&p->d_rtw, real_twiddles(cols))) != cudaSuccess) return cuda_fail(e, "twiddles");
+  if ((e = upload(&p->d_tw_cols, pass_table(rows, col_E(rows)))) != cudaSuccess) return cuda_fail(e, "twiddles");
 
   // supports
   if ((e = cudaMalloc(&p->d_planes, p->planes.size() * sizeof(PlaneDesc))) != cudaSuccess)
@@ -263,6 +346,7 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
     if (e == cudaSuccess) e = cudaMemcpy(mm.data(), d_mm, mm.size() * sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(d_mm);
     if (e != cudaSuccess) return cuda_fail(e, "ffst_plan support kernel");
+    int rng_total = 0;
     for (int i = 0; i < p->eta; ++i) {
       if (mm[2 * i + 1] < 0) {
         p->planes[i].c0 = 0;
@@ -271,7 +355,15 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
         p->planes[i].c0 = mm[2 * i];
         p->planes[i].W = mm[2 * i + 1] - mm[2 * i] + 1;
       }
+      p->planes[i].rng_off = rng_total;
+      rng_total += p->planes[i].W;
     }
+    // per-column row ranges of every plane's support
+    if ((e = cudaMalloc(&p->d_rng, (size_t)(rng_total > 0 ? rng_total : 1) * sizeof(int2))) != cudaSuccess)
+      return cuda_fail(e, "row ranges");
+    cudaMemcpy(p->d_planes, p->planes.data(), p->planes.size() * sizeof(PlaneDesc), cudaMemcpyHostToDevice);
+    e = launch_ranges(p.get(), 0);
+    if (e != cudaSuccess) return cuda_fail(e, "ffst_plan row ranges");
   }
 
   // groups and forward column work items
@@ -313,8 +405,9 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
   const size_t spec = (size_t)rows * p->Hc;
   if ((e = cudaMalloc(&p->d_F, spec * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "workspace F");
   if ((e = cudaMalloc(&p->d_S, spec * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "workspace S");
-  if ((e = cudaMalloc(&p->d_D, spec * sizeof(float))) != cudaSuccess) return cuda_fail(e, "workspace D");
-  if (p->h_elems > 0 && (e = cudaMalloc(&p->d_H, (size_t)p->h_elems * sizeof(float2))) != cudaSuccess)
+  if ((e = cudaMalloc(&p->d_invD, spec * sizeof(float))) != cudaSuccess) return cuda_fail(e, "normalisation");
+  if ((e = launch_inv_norm(p.get(), 0)) != cudaSuccess) return cuda_fail(e, "ffst_plan normalisation");
+  if (p->h_elems > 0 && (e = cudaMalloc(&p->d_H, 2 * (size_t)p->h_elems * sizeof(float2))) != cudaSuccess)
     return cuda_fail(e, "workspace H");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "ffst_plan");
   *out = p.release();
