@@ -65,10 +65,10 @@ __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c
 // thread of long row lines, and the minimum resident blocks per SM the
 // compiler must allow for (caps registers per thread at 65536/(256*n)).
 #ifndef FFST_ROW_E_LONG
-#define FFST_ROW_E_LONG 32
+#define FFST_ROW_E_LONG 16
 #endif
 #ifndef FFST_MIN_BLOCKS
-#define FFST_MIN_BLOCKS 1
+#define FFST_MIN_BLOCKS 4
 #endif
 __host__ __device__ constexpr int row_E(int L) { return L >= 1024 ? FFST_ROW_E_LONG : (L >= 16 ? 16 : L); }
 __host__ __device__ constexpr int col_E(int L) { return L >= 4096 ? 32 : (L >= 16 ? 16 : L); }

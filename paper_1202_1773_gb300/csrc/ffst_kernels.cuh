@@ -34,21 +34,23 @@ namespace ffst {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int stor_bytes(int st) { return st == FFST_STORE_F32 ? 4 : 2; }
 
+// Stack and image rows are touched once per transform: loads and stores use
+// the streaming (evict-first) cache policy so they do not push the plane
+// group intermediates out of L2.
 __device__ __forceinline__ float2 load_pair(const void* p, long long i, int st) {  // elements i, i+1 (i even)
-  if (st == FFST_STORE_F32)
-    return __ldg(reinterpret_cast<const float2*>(static_cast<const float*>(p) + i));
+  if (st == FFST_STORE_F32) return __ldcs(reinterpret_cast<const float2*>(static_cast<const float*>(p) + i));
   if (st == FFST_STORE_F16)
-    return __half22float2(*reinterpret_cast<const __half2*>(static_cast<const __half*>(p) + i));
-  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(static_cast<const __nv_bfloat16*>(p) + i));
+    return __half22float2(__ldcs(reinterpret_cast<const __half2*>(static_cast<const __half*>(p) + i)));
+  return __bfloat1622float2(__ldcs(reinterpret_cast<const __nv_bfloat162*>(static_cast<const __nv_bfloat16*>(p) + i)));
 }
 
 __device__ __forceinline__ void store_pair(void* p, long long i, float a, float b, int st) {
   if (st == FFST_STORE_F32)
-    *reinterpret_cast<float2*>(static_cast<float*>(p) + i) = make_float2(a, b);
+    __stcs(reinterpret_cast<float2*>(static_cast<float*>(p) + i), make_float2(a, b));
   else if (st == FFST_STORE_F16)
-    *reinterpret_cast<__half2*>(static_cast<__half*>(p) + i) = __floats2half2_rn(a, b);
+    __stcs(reinterpret_cast<__half2*>(static_cast<__half*>(p) + i), __floats2half2_rn(a, b));
   else
-    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(p) + i) = __floats2bfloat162_rn(a, b);
+    __stcs(reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(p) + i), __floats2bfloat162_rn(a, b));
 }
 
 // ---------------------------------------------------------------------------
@@ -132,7 +134,7 @@ __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, 
     const float2 e = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
     const float2 o = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
     const float2 w = __ldg(&a.rtw[k]);
-    drow[idx] = make_float2(e.x + w.x * o.x - w.y * o.y, e.y + w.x * o.y + w.y * o.x);
+    __stcg(&drow[idx], make_float2(e.x + w.x * o.x - w.y * o.y, e.y + w.x * o.y + w.y * o.x));
   }
 }
 
@@ -176,8 +178,8 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
   for (int m = 0; m < E; ++m) {
     const int k = t + T * m;
     const int ia = k - c0, ib = L - k - c0;
-    float2 xa = (act && (unsigned)ia < (unsigned)W) ? srow[ia] : make_float2(0.f, 0.f);
-    float2 xb = (act && (unsigned)ib < (unsigned)W) ? srow[ib] : make_float2(0.f, 0.f);
+    float2 xa = (act && (unsigned)ia < (unsigned)W) ? __ldcg(&srow[ia]) : make_float2(0.f, 0.f);
+    float2 xb = (act && (unsigned)ib < (unsigned)W) ? __ldcg(&srow[ib]) : make_float2(0.f, 0.f);
     if (k == 0) {  // X[0] and X[N/2]: Hermitian part is real
       xa.y = 0.f;
       xb.y = 0.f;
@@ -211,18 +213,20 @@ __device__ __forceinline__ void cols_fft_body(float2* __restrict__ buf, int widt
   const int t = threadIdx.x / P, cl = threadIdx.x % P;
   const int c = bx * P + cl;
   const bool act = c < width;
+  float2* col = buf + (long long)t * ld + c;  // element (t + T m, c) at col[m * T * ld]
+  const long long step = (long long)T * ld;
   float2 v[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const long long at = (long long)(t + T * m) * ld + c;
-    float2 x = act ? buf[at] : make_float2(0.f, 0.f);
-    if (scale_tab && act) x = cscale(x, __ldg(&scale_tab[at]));
-    v[m] = x;
+  for (int m = 0; m < E; ++m) v[m] = act ? col[m * step] : make_float2(0.f, 0.f);
+  if (scale_tab && act) {
+    const float* sc = scale_tab + (long long)t * ld + c;
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = cscale(v[m], __ldg(&sc[m * step]));
   }
   line_fft<L, E, INV, kSyncBlock>(v, smem + cl * ColCfg<L>::BUF, t, tw);
   if (act) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) buf[(long long)(t + T * m) * ld + c] = v[m];
+    for (int m = 0; m < E; ++m) col[m * step] = v[m];
   }
 }
 
@@ -292,7 +296,7 @@ __device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int item, fl
   if (act) {
     float2* out = a.H + d.off + (c - d.c0);
 #pragma unroll
-    for (int m = 0; m < E; ++m) out[(long long)(t + T * m) * d.W] = v[m];
+    for (int m = 0; m < E; ++m) __stcg(&out[(long long)(t + T * m) * d.W], v[m]);
   }
 }
 
@@ -327,7 +331,7 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
     const float2* in = a.H + d.off + (c - d.c0);
     float2 v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = act ? in[(long long)(t + T * m) * d.W] : make_float2(0.f, 0.f);
+    for (int m = 0; m < E; ++m) v[m] = act ? __ldcg(&in[(long long)(t + T * m) * d.W]) : make_float2(0.f, 0.f);
     const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
     line_fft<L, E, false, kSyncBlock>(v, buf, t, a.tw);
 #pragma unroll

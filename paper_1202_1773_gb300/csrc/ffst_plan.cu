@@ -206,10 +206,12 @@ static void free_plan(ffst_plan_s* p) {
 }
 
 // Intermediate budget per plane group.  The column pass writes a group's
-// intermediates and the row pass reads them back; two groups are in flight
-// (double buffer), so 2 x 32 MB plus F and S stay within the 126 MB L2.
+// intermediates and the row pass reads them back (two groups in flight,
+// double-buffered); the stack streams past L2 with evict-first hints, so the
+// intermediates mostly stay on chip.  Larger groups mean fewer launches and
+// shorter tails; 96 MB measured best at 2048x2048 (FFST_GROUP_MB overrides).
 static long long group_budget_elems() {
-  double mb = 32.0;
+  double mb = 96.0;
   if (const char* e = std::getenv("FFST_GROUP_MB")) {
     const double v = std::atof(e);
     if (v > 0.0) mb = v;
