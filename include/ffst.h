@@ -30,9 +30,11 @@
  *    host before anything is enqueued; FFST_ERR_CUDA reports a failed CUDA
  *    runtime call (launch or allocation), after which the outputs are
  *    unspecified.
- *  - Supported sizes: rows and cols are powers of two with 8 <= rows, cols
- *    <= 4096; scales in 1..8 (or <= 0 for the default j0 of Sec. 3.1).
- *    Other sizes return FFST_ERR_UNSUPPORTED_SIZE.
+ *  - Supported sizes: rows and cols even, 8 <= rows, cols <= 4096, rows a
+ *    power of two or one of 240, 320, 384, 480, 640, 768 (factors 2, 3, 5),
+ *    cols/2 a power of two or one of those (so 480x640 and 768x1024 work);
+ *    scales in 1..8 (or <= 0 for the default j0 of Sec. 3.1).  Other sizes
+ *    return FFST_ERR_UNSUPPORTED_SIZE.
  */
 #ifndef FFST_H
 #define FFST_H

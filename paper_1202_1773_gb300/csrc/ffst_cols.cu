@@ -36,6 +36,12 @@ int cols_per_cta(int L) {
     case 1024: return ColCfg<1024>::P;
     case 2048: return ColCfg<2048>::P;
     case 4096: return ColCfg<4096>::P;
+    case 240: return ColCfg<240>::P;
+    case 320: return ColCfg<320>::P;
+    case 384: return ColCfg<384>::P;
+    case 480: return ColCfg<480>::P;
+    case 640: return ColCfg<640>::P;
+    case 768: return ColCfg<768>::P;
     default: return 0;
   }
 }
@@ -84,6 +90,12 @@ static cudaError_t inv_cols_L(const InvColsArgs& a, int npanels, cudaStream_t s)
     case 1024: return CALL(1024);          \
     case 2048: return CALL(2048);          \
     case 4096: return CALL(4096);          \
+    case 240: return CALL(240);            \
+    case 320: return CALL(320);            \
+    case 384: return CALL(384);            \
+    case 480: return CALL(480);            \
+    case 640: return CALL(640);            \
+    case 768: return CALL(768);            \
     default: return cudaErrorInvalidValue; \
   }
 

@@ -63,6 +63,20 @@ __device__ __forceinline__ float2 twiddle_c(float2 x) {
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2 (&x)[R]) {
   if constexpr (R == 1) {
+  } else if constexpr (R == 3 || R == 5) {
+    // odd radices of mixed-radix lines: the DFT sum with constant roots
+    float2 y[R];
+    static_for<0, R>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      float2 acc = x[0];
+      static_for<1, R>([&](auto nc) {
+        constexpr int n = decltype(nc)::value;
+        acc = cadd(acc, twiddle_c<R, n * k, INV>(x[n]));
+      });
+      y[k] = acc;
+    });
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = y[k];
   } else if constexpr (R == 2) {
     const float2 a = x[0], b = x[1];
     x[0] = cadd(a, b);
@@ -115,7 +129,7 @@ __device__ __forceinline__ int spad(int i) {
 // rounded so that (stride mod 16) == skew; consecutive team buffers then
 // start on different banks (skew chosen by the kernel's lane layout).
 __host__ __device__ constexpr int team_stride(int L, int E, int skew) {
-  const int base = L + L / E;
+  const int base = is_pow2c(L) ? L + L / E : 2 * L;
   return base + ((skew - base % 16) % 16 + 16) % 16;
 }
 
@@ -181,12 +195,63 @@ __device__ __forceinline__ void stockham(float2 (&v)[E], float2* buf, int t, con
   }
 }
 
+// Mixed-radix lines (L not a power of two): the same Stockham passes, with
+// the data in shared memory between all passes (ping-pong between buf[0, L)
+// and buf[L, 2L)); NT threads share each pass's butterflies.
+template <int L, int E, bool INV, int Ns, int SYNC, int NT>
+__device__ __forceinline__ void mixed_passes(float2* a, float2* b, int t, const float2* __restrict__ tw, int bar) {
+  if constexpr (Ns < L) {
+    constexpr int R = next_radix(L, E, Ns);
+    constexpr int NB = L / R;
+    for (int j = t; j < NB; j += NT) {
+      float2 x[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = a[j + r * NB];
+      const int kk = j % Ns;
+      if constexpr (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = __ldg(&tw[(Ns - 1) + (r - 1) * Ns + kk]);
+          if (INV) w.y = -w.y;
+          x[r] = cmul(x[r], w);
+        }
+      }
+      dft<R, INV>(x);
+      const int base = (j / Ns) * Ns * R + kk;
+#pragma unroll
+      for (int r = 0; r < R; ++r) b[base + r * Ns] = x[r];
+    }
+    team_sync<SYNC, NT>(bar);
+    mixed_passes<L, E, INV, Ns * R, SYNC, NT>(b, a, t, tw, bar);
+  }
+}
+
 // Full line FFT (unnormalised).  Forward: X[k] = sum x[n] e^{-2 pi i nk/L};
-// inverse: the same with e^{+2 pi i nk/L}.
+// inverse: the same with e^{+2 pi i nk/L}.  Mixed-radix lines need a team
+// buffer of 2L slots.
 template <int L, int E, bool INV, int SYNC>
 __device__ __forceinline__ void line_fft(float2 (&v)[E], float2* buf, int t, const float2* __restrict__ tw,
                                          int bar = 0) {
-  stockham<L, E, INV, 1, SYNC>(v, buf, t, tw, bar);
+  if constexpr (is_pow2c(L)) {
+    stockham<L, E, INV, 1, SYNC>(v, buf, t, tw, bar);
+  } else {
+    constexpr int T = L / E;
+#pragma unroll
+    for (int m = 0; m < E; ++m) buf[t + T * m] = v[m];
+    team_sync<SYNC, T>(bar);
+    mixed_passes<L, E, INV, 1, SYNC, T>(buf, buf + L, t, tw, bar);
+    const float2* res = (num_passes(L, E) % 2 == 0) ? buf : buf + L;
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = res[t + T * m];
+    team_sync<SYNC, T>(bar);
+  }
+}
+
+// i mod L for i in [-L, 2L)
+template <int L>
+__device__ __forceinline__ int mod_l(int i) {
+  if constexpr (is_pow2c(L)) return i & (L - 1);
+  else return i < 0 ? i + L : (i >= L ? i - L : i);
 }
 
 }  // namespace ffst

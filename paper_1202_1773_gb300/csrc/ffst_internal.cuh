@@ -70,8 +70,44 @@ __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c
 #ifndef FFST_MIN_BLOCKS
 #define FFST_MIN_BLOCKS 4
 #endif
-__host__ __device__ constexpr int row_E(int L) { return L >= 1024 ? FFST_ROW_E_LONG : (L >= 16 ? 16 : L); }
-__host__ __device__ constexpr int col_E(int L) { return L >= 4096 ? 32 : (L >= 16 ? 16 : L); }
+__host__ __device__ constexpr bool is_pow2c(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Line lengths with factors 3 or 5 (mixed radix) run 16 or 32 threads per
+// line; powers of two use the register configuration below.
+__host__ __device__ constexpr int mixed_E(int L) { return L / (L <= 256 ? 16 : 32); }
+__host__ __device__ constexpr int row_E(int L) {
+  return !is_pow2c(L) ? mixed_E(L) : (L >= 1024 ? FFST_ROW_E_LONG : (L >= 16 ? 16 : L));
+}
+__host__ __device__ constexpr int col_E(int L) {
+  return !is_pow2c(L) ? mixed_E(L) : (L >= 4096 ? 32 : (L >= 16 ? 16 : L));
+}
+
+// Radix of the pass of a line of length L that starts at sub-transform
+// length Ns: min(E, L/Ns) for powers of two; otherwise the largest of
+// 16, 8, 4, 2 dividing what is left, then 3, then 5.
+__host__ __device__ constexpr int next_radix(int L, int E, int Ns) {
+  const int rem = L / Ns;
+  if (is_pow2c(L)) return rem < E ? rem : E;
+  if (rem % 16 == 0) return 16;
+  if (rem % 8 == 0) return 8;
+  if (rem % 4 == 0) return 4;
+  if (rem % 2 == 0) return 2;
+  if (rem % 3 == 0) return 3;
+  return 5;
+}
+
+__host__ __device__ constexpr int num_passes(int L, int E) {
+  int n = 0;
+  for (int Ns = 1; Ns < L; Ns *= next_radix(L, E, Ns)) ++n;
+  return n;
+}
+
+// Line lengths the kernels are built for: powers of two 4..4096 and
+// 240, 320, 384, 480, 640, 768 (factors 2, 3, 5).
+__host__ __device__ constexpr bool supported_line(int L) {
+  return (is_pow2c(L) && L >= 4 && L <= 4096) || L == 240 || L == 320 || L == 384 || L == 480 || L == 640 ||
+         L == 768;
+}
 
 // Every transform kernel runs 256-thread blocks, so a row-pass block and a
 // column-pass block can share one fused launch.
@@ -84,7 +120,7 @@ constexpr int kThreads = 256;
 __host__ __device__ inline void pass_entry(int L, int E, int idx, int* m, int* n) {
   int Ns = 1;
   while (Ns < L) {
-    const int R = (L / Ns) < E ? (L / Ns) : E;
+    const int R = next_radix(L, E, Ns);
     if (idx < Ns * R - 1) {
       const int q = idx - (Ns - 1);
       *m = (q % Ns) * (q / Ns + 1);

@@ -58,6 +58,7 @@ __device__ __forceinline__ void store_pair(void* p, long long i, float a, float 
 // ---------------------------------------------------------------------------
 template <int L>
 struct RowCfg {
+  static_assert(supported_line(L), "unsupported row line length");
   static constexpr int E = row_E(L);
   static constexpr int T = L / E;
   static constexpr int TEAMS = (T >= kThreads) ? 1 : kThreads / T;  // rows per block
@@ -69,6 +70,7 @@ struct RowCfg {
 
 template <int L>
 struct ColCfg {
+  static_assert(supported_line(L), "unsupported column length");
   static constexpr int E = col_E(L);
   static constexpr int T = L / E;
   static constexpr int P = kThreads / T;  // columns per block
@@ -77,7 +79,10 @@ struct ColCfg {
   static_assert(P * T == kThreads, "column teams must fill the block");
 };
 
-__device__ __forceinline__ bool in_range(int row, int2 rg, int M) { return ((row - rg.x) & (M - 1)) < rg.y; }
+template <int M>
+__device__ __forceinline__ bool in_range(int row, int2 rg) {
+  return mod_l<M>(row - rg.x) < rg.y;
+}
 
 // ---------------------------------------------------------------------------
 // row passes
@@ -129,8 +134,8 @@ __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, 
   float2* drow = dst + (long long)row * ld;
   for (int idx = t; idx < W; idx += T) {
     const int k = c0 + idx;  // 0 .. L
-    const float2 zk = buf[spad<E>(k & (L - 1))];
-    const float2 zn = buf[spad<E>((L - k) & (L - 1))];
+    const float2 zk = buf[spad<E>(mod_l<L>(k))];
+    const float2 zn = buf[spad<E>(mod_l<L>(L - k))];
     const float2 e = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
     const float2 o = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
     const float2 w = __ldg(&a.rtw[k]);
@@ -265,7 +270,7 @@ __device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int item, fl
   const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
   float mag = 0.0f;
   for (int q = t; q < rg.y; q += T) {
-    const int row = (rg.x + q) & (L - 1);
+    const int row = mod_l<L>(rg.x + q);
     const float psi = win_at(a.w, d, row, c);
     float2 g = make_float2(0.f, 0.f);
     if (psi != 0.0f) g = cscale(a.F[(long long)row * a.Hc + c], psi);
@@ -277,7 +282,7 @@ __device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int item, fl
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int row = t + T * m;
-    v[m] = in_range(row, rg, L) ? buf[spad<E>(row)] : make_float2(0.f, 0.f);
+    v[m] = in_range<L>(row, rg) ? buf[spad<E>(row)] : make_float2(0.f, 0.f);
   }
   if (a.partials) {
     const bool self_partner = (c == 0) || (2 * c == a.w.N);
@@ -337,11 +342,11 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int row = t + T * m;
-      if (in_range(row, rg, L)) buf[spad<E>(row)] = v[m];
+      if (in_range<L>(row, rg)) buf[spad<E>(row)] = v[m];
     }
     __syncthreads();
     for (int q = t; q < rg.y; q += T) {
-      const int row = (rg.x + q) & (L - 1);
+      const int row = mod_l<L>(rg.x + q);
       const float psi = win_at(a.w, d, row, c);
       const float2 x = buf[spad<E>(row)];
       float2* sp = a.S + (long long)row * a.Hc + c;

@@ -141,7 +141,9 @@ __global__ void k_inv_norm(WinParams w, const PlaneDesc* __restrict__ planes, in
       const int q = pc - d.c0;
       if (q < 0 || q >= d.W) continue;
       const int2 rg = rng[d.rng_off + q];
-      if (((pr - rg.x) & (w.M - 1)) >= rg.y) continue;
+      int off = pr - rg.x;
+      if (off < 0) off += w.M;
+      if (off >= rg.y) continue;
       const float psi = win_at(w, d, pr, pc);
       sum = fmaf(psi, psi, sum);
     }
@@ -180,8 +182,6 @@ ffst_status cuda_fail(cudaError_t e, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? FFST_ERR_OUT_OF_MEMORY : FFST_ERR_CUDA;
 }
-
-static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 static void free_plan(ffst_plan_s* p) {
   if (!p) return;
@@ -254,9 +254,12 @@ using namespace ffst;
 extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* out) {
   if (!out) return fail(FFST_ERR_INVALID_ARG, "ffst_plan: out is NULL");
   *out = nullptr;
-  if (!is_pow2(rows) || !is_pow2(cols) || rows < 8 || cols < 8 || rows > 4096 || cols > 4096)
-    return fail(FFST_ERR_UNSUPPORTED_SIZE, "ffst_plan: rows and cols must be powers of two in [8, 4096], got " +
-                                               std::to_string(rows) + "x" + std::to_string(cols));
+  if (rows < 8 || cols < 8 || rows > 4096 || cols > 4096 || rows % 2 || cols % 2 || !supported_line(rows) ||
+      !supported_line(cols / 2))
+    return fail(FFST_ERR_UNSUPPORTED_SIZE,
+                "ffst_plan: rows must be a power of two in [8, 4096] or one of 240, 320, 384, 480, 640, 768, and "
+                "cols/2 a power of two in [4, 2048] or one of those, got " +
+                    std::to_string(rows) + "x" + std::to_string(cols));
   const int mx = rows > cols ? rows : cols;
   int lg = 0;
   while ((1 << (lg + 1)) <= mx) ++lg;

@@ -46,6 +46,12 @@ static cudaError_t c2r_L(const C2RArgs& a, int nplanes, cudaStream_t s) {
     case 512: return CALL(512);            \
     case 1024: return CALL(1024);          \
     case 2048: return CALL(2048);          \
+    case 240: return CALL(240);            \
+    case 320: return CALL(320);            \
+    case 384: return CALL(384);            \
+    case 480: return CALL(480);            \
+    case 640: return CALL(640);            \
+    case 768: return CALL(768);            \
     default: return cudaErrorInvalidValue; \
   }
 

@@ -121,4 +121,5 @@ def test_deconvolution_1024_gradient(ffst):
     y64 = y.astype(np.float64)
     gr = do.gradient(y64, y64, psf, lam, eps, None)
     assert _rel(g.cpu().numpy(), gr) <= 1e-4
-    assert abs(float(J) - do.objective(y64, y64, psf, lam, eps, None)) <= 1e-4 * abs(float(J))
+    Jv = float(J.detach())
+    assert abs(Jv - do.objective(y64, y64, psf, lam, eps, None)) <= 1e-4 * abs(Jv)

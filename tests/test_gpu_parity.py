@@ -187,3 +187,33 @@ def test_errors_reported(ffst):
         _lib.ffst_forward(plan.handle, x, c.half(), _lib.FFST_STORE_F16, None, None)  # scales required
     with pytest.raises(ffst.FFSTError):
         _lib.ffst_plane_index(plan.handle, plan.num_planes)
+
+
+# mixed-radix sizes (factors 3 and 5): the uneven sizes of the batched workload
+@pytest.mark.parametrize("shape", [(240, 480), (480, 640), (640, 480), (320, 640), (384, 256), (64, 768)])
+def test_mixed_radix_sizes_match_oracle(ffst, shape):
+    f = _img(*shape, seed=11)
+    plan = ffst.Plan(*shape)
+    x = torch.from_numpy(f).cuda()
+    c = plan.forward(x)
+    ref = o.forward(f.astype(np.float64))
+    assert rel_l2(c.cpu().numpy(), ref) <= FP32_TOL
+    rec = plan.inverse(c).cpu().numpy()
+    assert rel_l2(rec, f) <= FP32_TOL
+    psi = plan.spectra().cpu().numpy()
+    assert np.abs(psi - o.spectra(*shape)).max() <= 1e-6
+
+
+def test_mixed_radix_768x1024_sampled(ffst):
+    shape = (768, 1024)
+    f = inputs.scaled_cartoon(*shape, seed=12)
+    plan = ffst.Plan(*shape)
+    x = torch.from_numpy(f).cuda()
+    c = plan.forward(x)
+    F = np.fft.fft2(f.astype(np.float64))
+    for i in [0, 3, 20, 64, 100, 124]:
+        ref = o.forward_plane(F, plan.scales, i)
+        err = np.linalg.norm(c[i].cpu().numpy() - ref) / max(np.linalg.norm(ref), 1e-3 * np.linalg.norm(f))
+        assert err <= FP32_TOL, (i, err)
+    rec = plan.inverse(c)
+    assert float(torch.linalg.norm(rec - x) / torch.linalg.norm(x)) <= FP32_TOL
