@@ -148,6 +148,58 @@ ffst_status ffst_adjoint(ffst_plan_t plan, const void* coeffs, int storage,
  */
 ffst_status ffst_forward_noalloc(int rows, int cols, int scales, const float* img, float* coeffs, void* stream);
 
+/*
+ * Autotune a plan's launch configuration for coefficient storage `storage`:
+ * times `reps` forward + inverse round trips (after one warm-up) for each
+ * candidate plane-group budget (16, 32, 64, 96, 128 MB of column-pass
+ * intermediates per fused launch) and keeps the fastest.  Allocates a
+ * temporary image and coefficient stack of the plan's size (eta*rows*cols
+ * elements) and synchronises the device.  When the environment variable
+ * FFST_AUTOTUNE_CACHE names a file, the choice is appended to it and later
+ * ffst_plan calls for the same device and shape start from it.  Results do
+ * not depend on the budget.  *chosen_mb (may be NULL) receives the choice.
+ */
+ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int reps, double* chosen_mb);
+
+/* The plane-group budget (MB) the plan currently uses. */
+ffst_status ffst_plan_group_mb(ffst_plan_t plan, double* mb);
+
+/*
+ * Batches of images of uneven sizes.  ffst_plan_batched builds one plan per
+ * (size, lane) for n images (rows[i] x cols[i], scales[i] <= 0 or NULL for
+ * the default) and spreads the images over `lanes` (1..16) internal streams,
+ * largest transform first onto the least loaded lane, so transforms of
+ * different images run concurrently.  The batched calls fork the lanes from
+ * `stream` and join them back before returning control of the stream:
+ *   imgs[i], coeffs[i], plane_scales[i] are device pointers as in
+ *   ffst_forward / ffst_inverse, passed as host arrays of n pointers
+ *   (plane_scales may be NULL for F32 storage).
+ * Calls on one batch must not overlap (lanes share plan workspaces).
+ */
+typedef struct ffst_batch_s* ffst_batch_t;
+ffst_status ffst_plan_batched(int n, const int* rows, const int* cols, const int* scales, int lanes,
+                              ffst_batch_t* out);
+/* Image i's size, scales, planes and lane.  Any output may be NULL. */
+ffst_status ffst_batch_info(ffst_batch_t batch, int i, int* rows, int* cols, int* scales, int* num_planes, int* lane);
+ffst_status ffst_forward_batched(ffst_batch_t batch, const float* const* imgs, void* const* coeffs, int storage,
+                                 float* const* plane_scales, void* stream);
+ffst_status ffst_inverse_batched(ffst_batch_t batch, const void* const* coeffs, int storage,
+                                 float* const* plane_scales, float* const* imgs, void* stream);
+void ffst_batch_destroy(ffst_batch_t batch);
+
+/*
+ * Capture a batched forward (what bit 0) and/or inverse (bit 1, from the
+ * same coeffs into out_imgs) into one instantiated CUDA graph.  Runs the
+ * work once eagerly first (module loading, kernel attributes), then
+ * captures it on an internal stream.  The pointers are baked into the graph;
+ * ffst_graph_launch replays it on `stream`, ffst_graph_destroy frees it.
+ */
+ffst_status ffst_graph_capture_batched(ffst_batch_t batch, int what, const float* const* imgs, void* const* coeffs,
+                                       int storage, float* const* plane_scales, float* const* out_imgs,
+                                       void** graph_exec);
+ffst_status ffst_graph_launch(void* graph_exec, void* stream);
+void ffst_graph_destroy(void* graph_exec);
+
 /* Free a plan and everything it owns (synchronises the device first).  NULL is a no-op. */
 void ffst_destroy(ffst_plan_t plan);
 

@@ -29,7 +29,17 @@ from ._lib import (  # noqa: F401
     FFST_STORE_F32,
     FFSTError,
     ffst_adjoint,
+    ffst_batch_destroy,
+    ffst_batch_info,
     ffst_destroy,
+    ffst_forward_batched,
+    ffst_graph_capture_batched,
+    ffst_graph_destroy,
+    ffst_graph_launch,
+    ffst_inverse_batched,
+    ffst_plan_autotune,
+    ffst_plan_batched,
+    ffst_plan_group_mb,
     ffst_forward,
     ffst_forward_noalloc,
     ffst_inverse,
@@ -43,7 +53,7 @@ from ._lib import (  # noqa: F401
     ffst_timing_reset,
 )
 
-__all__ = ["Plan", "FFSTFunction", "shearlet_transform", "FFSTError"] + [n for n, _, _ in _lib.SIGNATURES]
+__all__ = ["Plan", "BatchPlan", "Graph", "FFSTFunction", "shearlet_transform", "FFSTError"] + [n for n, _, _ in _lib.SIGNATURES]
 
 
 def _torch():
@@ -155,6 +165,17 @@ class Plan:
     def adjoint(self, coeffs, plane_scale=None, out=None):
         return self._synth(ffst_adjoint, coeffs, plane_scale, out)
 
+    # -- tuning ---------------------------------------------------------------
+    def autotune(self, dtype=None, reps: int = 3) -> float:
+        """Measure the plane-group budgets and keep the fastest (see ffst_plan_autotune)."""
+        torch = _torch()
+        with torch.cuda.device(self.device):
+            return ffst_plan_autotune(self.handle, _storage_of(dtype or torch.float32), reps)
+
+    @property
+    def group_mb(self) -> float:
+        return ffst_plan_group_mb(self.handle)
+
     # -- timing ---------------------------------------------------------------
     def timing(self, enable: bool):
         ffst_timing_enable(self.handle, enable)
@@ -169,6 +190,97 @@ class Plan:
             name, ms, n, by = ffst_timing_read(self.handle, k)
             out[name] = (ms, n, by)
         return out
+
+
+class Graph:
+    """An instantiated CUDA graph of batched transforms (ffst_graph_capture_batched)."""
+
+    def __init__(self, handle: int, device, keep):
+        self.handle = handle
+        self.device = device
+        self._keep = keep  # the tensors whose addresses are baked into the graph
+
+    def launch(self, stream=None):
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream(self.device).cuda_stream
+        ffst_graph_launch(self.handle, s)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ffst_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchPlan:
+    """Transforms of a batch of images of uneven sizes (ffst_plan_batched)."""
+
+    def __init__(self, shapes, scales=None, lanes: int = 4, device=None):
+        torch = _torch()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        rows = [r for r, _ in shapes]
+        cols = [c for _, c in shapes]
+        with torch.cuda.device(self.device):
+            self.handle = ffst_plan_batched(rows, cols, scales, lanes)
+        self.info = [ffst_batch_info(self.handle, i) for i in range(len(shapes))]
+
+    def __len__(self):
+        return len(self.info)
+
+    def shape(self, i):
+        r, c, _, eta, _ = self.info[i]
+        return (eta, r, c)
+
+    def lanes(self):
+        return [x[4] for x in self.info]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ffst_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        return _torch().cuda.current_stream(self.device).cuda_stream
+
+    def empty_stacks(self, dtype=None):
+        torch = _torch()
+        return [torch.empty(self.shape(i), dtype=dtype or torch.float32, device=self.device) for i in range(len(self))]
+
+    def forward(self, imgs, outs=None, dtype=None, plane_scales=None):
+        torch = _torch()
+        outs = outs if outs is not None else self.empty_stacks(dtype)
+        storage = _storage_of(outs[0].dtype)
+        if storage != FFST_STORE_F32 and plane_scales is None:
+            plane_scales = [torch.empty(self.shape(i)[0], device=self.device) for i in range(len(self))]
+        ffst_forward_batched(self.handle, imgs, outs, storage, plane_scales if storage != FFST_STORE_F32 else None,
+                             self._stream())
+        return (outs, plane_scales) if storage != FFST_STORE_F32 else outs
+
+    def inverse(self, stacks, plane_scales=None, outs=None):
+        torch = _torch()
+        outs = outs if outs is not None else [
+            torch.empty(self.shape(i)[1:], device=self.device) for i in range(len(self))]
+        ffst_inverse_batched(self.handle, stacks, _storage_of(stacks[0].dtype), plane_scales, outs, self._stream())
+        return outs
+
+    def capture(self, imgs, stacks, outs, what: int = 3, plane_scales=None) -> Graph:
+        """One CUDA graph of the batched forward (what & 1) and/or inverse (what & 2)."""
+        torch = _torch()
+        with torch.cuda.device(self.device):
+            h = ffst_graph_capture_batched(self.handle, what, imgs, stacks, _storage_of(stacks[0].dtype),
+                                           plane_scales, outs)
+        return Graph(h, self.device, (imgs, stacks, outs, plane_scales))
 
 
 def _make_autograd():

@@ -38,6 +38,19 @@ SIGNATURES = [
     ("ffst_inverse", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
     ("ffst_adjoint", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
     ("ffst_forward_noalloc", _I, [_I, _I, _I, _VP, _VP, _VP]),
+    ("ffst_plan_autotune", _I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_double)]),
+    ("ffst_plan_group_mb", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    ("ffst_plan_batched", _I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _I,
+                               ctypes.POINTER(_VP)]),
+    ("ffst_batch_info", _I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                             ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    ("ffst_forward_batched", _I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), _VP]),
+    ("ffst_inverse_batched", _I, [_VP, ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    ("ffst_batch_destroy", None, [_VP]),
+    ("ffst_graph_capture_batched", _I, [_VP, _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
+                                        ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    ("ffst_graph_launch", _I, [_VP, _VP]),
+    ("ffst_graph_destroy", None, [_VP]),
     ("ffst_destroy", None, [_VP]),
     ("ffst_last_error", ctypes.c_char_p, []),
     ("ffst_status_string", ctypes.c_char_p, [_I]),
@@ -145,6 +158,76 @@ def ffst_forward_noalloc(rows: int, cols: int, scales: int, img, coeffs, stream=
     """Allocation-free forward transform of a small image (see include/ffst.h)."""
     _check("ffst_forward_noalloc", lib().ffst_forward_noalloc(int(rows), int(cols), int(scales), _ptr(img),
                                                               _ptr(coeffs), stream))
+
+
+def ffst_plan_autotune(plan: int, storage: int = FFST_STORE_F32, reps: int = 3) -> float:
+    mb = ctypes.c_double()
+    _check("ffst_plan_autotune", lib().ffst_plan_autotune(plan, int(storage), int(reps), ctypes.byref(mb)))
+    return mb.value
+
+
+def ffst_plan_group_mb(plan: int) -> float:
+    mb = ctypes.c_double()
+    _check("ffst_plan_group_mb", lib().ffst_plan_group_mb(plan, ctypes.byref(mb)))
+    return mb.value
+
+
+def _ints(vals):
+    return (_I * len(vals))(*[int(v) for v in vals])
+
+
+def _ptrs(vals):
+    if vals is None:
+        return None
+    return (_VP * len(vals))(*[_ptr(v) for v in vals])
+
+
+def ffst_plan_batched(rows, cols, scales=None, lanes: int = 4) -> int:
+    out = _VP()
+    n = len(rows)
+    _check("ffst_plan_batched", lib().ffst_plan_batched(n, _ints(rows), _ints(cols),
+                                                        _ints(scales) if scales is not None else None, int(lanes),
+                                                        ctypes.byref(out)))
+    return out.value
+
+
+def ffst_batch_info(batch: int, i: int):
+    r, c, s, n, lane = _I(), _I(), _I(), _I(), _I()
+    _check("ffst_batch_info", lib().ffst_batch_info(batch, int(i), ctypes.byref(r), ctypes.byref(c), ctypes.byref(s),
+                                                    ctypes.byref(n), ctypes.byref(lane)))
+    return r.value, c.value, s.value, n.value, lane.value
+
+
+def ffst_forward_batched(batch: int, imgs, coeffs, storage: int = FFST_STORE_F32, plane_scales=None, stream=None):
+    _check("ffst_forward_batched", lib().ffst_forward_batched(batch, _ptrs(imgs), _ptrs(coeffs), int(storage),
+                                                              _ptrs(plane_scales), stream))
+
+
+def ffst_inverse_batched(batch: int, coeffs, storage: int, plane_scales, imgs, stream=None):
+    _check("ffst_inverse_batched", lib().ffst_inverse_batched(batch, _ptrs(coeffs), int(storage), _ptrs(plane_scales),
+                                                              _ptrs(imgs), stream))
+
+
+def ffst_batch_destroy(batch: int):
+    if batch:
+        lib().ffst_batch_destroy(batch)
+
+
+def ffst_graph_capture_batched(batch: int, what: int, imgs, coeffs, storage: int, plane_scales, out_imgs) -> int:
+    out = _VP()
+    _check("ffst_graph_capture_batched", lib().ffst_graph_capture_batched(
+        batch, int(what), _ptrs(imgs), _ptrs(coeffs), int(storage), _ptrs(plane_scales), _ptrs(out_imgs),
+        ctypes.byref(out)))
+    return out.value
+
+
+def ffst_graph_launch(graph_exec: int, stream=None):
+    _check("ffst_graph_launch", lib().ffst_graph_launch(graph_exec, stream))
+
+
+def ffst_graph_destroy(graph_exec: int):
+    if graph_exec:
+        lib().ffst_graph_destroy(graph_exec)
 
 
 def ffst_destroy(plan: int):

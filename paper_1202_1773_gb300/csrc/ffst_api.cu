@@ -27,6 +27,8 @@ static cudaEvent_t take_event(ffst_plan_s* p) {
 template <class F>
 static cudaError_t timed(ffst_plan_s* p, int kind, double bytes, cudaStream_t s, F&& launch) {
   if (!p->timer.enabled) return launch();
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone) return launch();
   cudaEvent_t a = take_event(p), b = take_event(p);
   cudaEventRecord(a, s);
   const cudaError_t e = launch();

@@ -223,6 +223,7 @@ struct ffst_plan_s {
   float* d_partials = nullptr;          // [total items] per-panel sums of |psi F| (low-precision storage)
   int total_items = 0;
   std::vector<ffst::Group> groups;
+  double group_mb = 0.0;                // budget the groups were built for
   ffst::ColItem* d_items = nullptr;
   ffst::Timer timer;
 };
@@ -233,6 +234,11 @@ namespace ffst {
 void set_error(const std::string& msg);
 ffst_status fail(ffst_status st, const std::string& msg);
 ffst_status cuda_fail(cudaError_t e, const char* what);
+
+// plan grouping and autotuning (ffst_plan.cu, ffst_autotune.cu)
+double default_group_mb();
+ffst_status plan_regroup(ffst_plan_s* p, double mb);
+bool autotune_lookup(const ffst_plan_s* p, int storage, double* mb);
 
 // timing helpers
 void timer_begin(ffst_plan_s* p, int kind, cudaStream_t s, double bytes, cudaEvent_t* out_b);

@@ -209,14 +209,66 @@ static void free_plan(ffst_plan_s* p) {
 // intermediates and the row pass reads them back (two groups in flight,
 // double-buffered); the stack streams past L2 with evict-first hints, so the
 // intermediates mostly stay on chip.  Larger groups mean fewer launches and
-// shorter tails; 96 MB measured best at 2048x2048 (FFST_GROUP_MB overrides).
-static long long group_budget_elems() {
+// shorter tails; 96 MB measured best at 2048x2048.  FFST_GROUP_MB overrides
+// the default; ffst_plan_autotune measures the candidates instead.
+double default_group_mb() {
   double mb = 96.0;
   if (const char* e = std::getenv("FFST_GROUP_MB")) {
     const double v = std::atof(e);
     if (v > 0.0) mb = v;
   }
-  return (long long)(mb * 1024.0 * 1024.0 / sizeof(float2));
+  return mb;
+}
+
+// (Re)build the plane groups, the forward column work items and the
+// double-buffered intermediate for a group budget of `mb` megabytes.
+ffst_status plan_regroup(ffst_plan_s* p, double mb) {
+  const long long budget = (long long)(mb * 1024.0 * 1024.0 / sizeof(float2));
+  const int P = cols_per_cta(p->M);
+  cudaFree(p->d_items);
+  cudaFree(p->d_partials);
+  cudaFree(p->d_H);
+  p->d_items = nullptr;
+  p->d_partials = nullptr;
+  p->d_H = nullptr;
+  p->groups.clear();
+  std::vector<ColItem> items;
+  Group g{0, 0, 0, 0, 0};
+  long long maxg = 0;
+  for (int i = 0; i < p->eta; ++i) {
+    const long long el = (long long)p->M * p->planes[i].W;
+    if (g.p1 > g.p0 && g.elems + el > budget) {
+      g.nitems = (int)items.size() - g.item0;
+      p->groups.push_back(g);
+      maxg = std::max(maxg, g.elems);
+      g = Group{i, i, 0, (int)items.size(), 0};
+    }
+    p->planes[i].off = g.elems;
+    p->planes[i].item0 = (int)items.size();
+    for (int c = p->planes[i].c0; c < p->planes[i].c0 + p->planes[i].W; c += P) items.push_back(ColItem{i, c});
+    p->planes[i].nitems = (int)items.size() - p->planes[i].item0;
+    g.elems += el;
+    g.p1 = i + 1;
+  }
+  g.nitems = (int)items.size() - g.item0;
+  p->groups.push_back(g);
+  maxg = std::max(maxg, g.elems);
+  p->h_elems = maxg;
+  p->group_mb = mb;
+  p->total_items = (int)items.size();
+  cudaError_t e = cudaMemcpy(p->d_planes, p->planes.data(), p->planes.size() * sizeof(PlaneDesc),
+                             cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "plane descriptors");
+  if (!items.empty()) {
+    if ((e = cudaMalloc(&p->d_items, items.size() * sizeof(ColItem))) != cudaSuccess) return cuda_fail(e, "items");
+    if ((e = cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(ColItem), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return cuda_fail(e, "items");
+    if ((e = cudaMalloc(&p->d_partials, items.size() * sizeof(float))) != cudaSuccess) return cuda_fail(e, "partials");
+  }
+  if (p->h_elems > 0 && (e = cudaMalloc(&p->d_H, 2 * (size_t)p->h_elems * sizeof(float2))) != cudaSuccess)
+    return cuda_fail(e, "workspace H");
+  return FFST_OK;
 }
 
 // Pass twiddle table of a line (L, E) (layout in ffst_fft.cuh), FP64 -> FP32.
@@ -371,39 +423,12 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
     if (e != cudaSuccess) return cuda_fail(e, "ffst_plan row ranges");
   }
 
-  // groups and forward column work items
-  const long long budget = group_budget_elems();
-  const int P = cols_per_cta(rows);
-  std::vector<ColItem> items;
+  // groups and forward column work items (budget: autotune cache, FFST_GROUP_MB, default)
   {
-    Group g{0, 0, 0, 0, 0};
-    long long maxg = 0;
-    for (int i = 0; i < p->eta; ++i) {
-      const long long el = (long long)rows * p->planes[i].W;
-      if (g.p1 > g.p0 && g.elems + el > budget) {
-        g.nitems = (int)items.size() - g.item0;
-        p->groups.push_back(g);
-        maxg = std::max(maxg, g.elems);
-        g = Group{i, i, 0, (int)items.size(), 0};
-      }
-      p->planes[i].off = g.elems;
-      p->planes[i].item0 = (int)items.size();
-      for (int c = p->planes[i].c0; c < p->planes[i].c0 + p->planes[i].W; c += P) items.push_back(ColItem{i, c});
-      p->planes[i].nitems = (int)items.size() - p->planes[i].item0;
-      g.elems += el;
-      g.p1 = i + 1;
-    }
-    g.nitems = (int)items.size() - g.item0;
-    p->groups.push_back(g);
-    maxg = std::max(maxg, g.elems);
-    p->h_elems = maxg;
-  }
-  p->total_items = (int)items.size();
-  cudaMemcpy(p->d_planes, p->planes.data(), p->planes.size() * sizeof(PlaneDesc), cudaMemcpyHostToDevice);
-  if (!items.empty()) {
-    if ((e = cudaMalloc(&p->d_items, items.size() * sizeof(ColItem))) != cudaSuccess) return cuda_fail(e, "items");
-    cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(ColItem), cudaMemcpyHostToDevice);
-    if ((e = cudaMalloc(&p->d_partials, items.size() * sizeof(float))) != cudaSuccess) return cuda_fail(e, "partials");
+    double mb = 0.0;
+    if (!autotune_lookup(p.get(), FFST_STORE_F32, &mb)) mb = default_group_mb();
+    const ffst_status st = plan_regroup(p.get(), mb);
+    if (st != FFST_OK) return st;
   }
 
   // workspace
@@ -412,8 +437,6 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
   if ((e = cudaMalloc(&p->d_S, spec * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "workspace S");
   if ((e = cudaMalloc(&p->d_invD, spec * sizeof(float))) != cudaSuccess) return cuda_fail(e, "normalisation");
   if ((e = launch_inv_norm(p.get(), 0)) != cudaSuccess) return cuda_fail(e, "ffst_plan normalisation");
-  if (p->h_elems > 0 && (e = cudaMalloc(&p->d_H, 2 * (size_t)p->h_elems * sizeof(float2))) != cudaSuccess)
-    return cuda_fail(e, "workspace H");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "ffst_plan");
   *out = p.release();
   return FFST_OK;

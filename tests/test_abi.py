@@ -66,3 +66,20 @@ def test_null_arguments_rejected_on_host(lib):
     lib.ffst_destroy(None)  # no-op
     with pytest.raises(_lib.FFSTError):
         _lib.ffst_plan(64, 48, 0)
+
+
+def test_batch_and_graph_argument_errors_on_host(lib):
+    out = ctypes.c_void_p()
+    rows = (ctypes.c_int * 1)(64)
+    cols = (ctypes.c_int * 1)(64)
+    assert lib.ffst_plan_batched(0, rows, cols, None, 4, ctypes.byref(out)) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_plan_batched(1, rows, cols, None, 0, ctypes.byref(out)) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_plan_batched(1, None, cols, None, 4, ctypes.byref(out)) == _lib.FFST_ERR_INVALID_ARG
+    bad = (ctypes.c_int * 1)(100)
+    assert lib.ffst_plan_batched(1, bad, cols, None, 4, ctypes.byref(out)) == _lib.FFST_ERR_UNSUPPORTED_SIZE
+    assert lib.ffst_batch_info(None, 0, None, None, None, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_forward_batched(None, None, None, 0, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_graph_launch(None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_plan_autotune(None, 0, 1, None) == _lib.FFST_ERR_INVALID_ARG
+    lib.ffst_graph_destroy(None)
+    lib.ffst_batch_destroy(None)

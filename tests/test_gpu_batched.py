@@ -1,0 +1,109 @@
+"""Batched transforms over uneven sizes, CUDA-graph replay and the autotuner.
+
+Every batched result must equal (bitwise) the same image through its own
+single plan: the batch only schedules the same kernels on several streams.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ffst_oracle as o
+from paper_1202_1773_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(128, 128), (256, 256), (480, 640), (512, 512), (768, 1024), (1024, 1024)]
+
+
+@pytest.fixture(scope="module")
+def ffst():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1202_1773_gb300 as pkg
+    from paper_1202_1773_gb300 import build
+
+    build.build()
+    return pkg
+
+
+def _batch(n, seed):
+    shapes = inputs.batch_sizes(n, seed=seed)
+    imgs = [torch.from_numpy(inputs.scaled_cartoon(r, c, seed=100 + i)).cuda() for i, (r, c) in enumerate(shapes)]
+    return shapes, imgs
+
+
+def test_batched_equals_single_plans(ffst):
+    shapes, imgs = _batch(12, seed=2)
+    bp = ffst.BatchPlan(shapes, lanes=4)
+    assert sorted(set(bp.lanes())) == [0, 1, 2, 3]
+    stacks = bp.forward(imgs)
+    recs = bp.inverse(stacks)
+    torch.cuda.synchronize()
+    for i, (r, c) in enumerate(shapes):
+        p = ffst.Plan(r, c)
+        ref = p.forward(imgs[i])
+        assert torch.equal(stacks[i], ref), i
+        assert torch.equal(recs[i], p.inverse(ref)), i
+        assert float(torch.linalg.norm(recs[i] - imgs[i]) / torch.linalg.norm(imgs[i])) <= 1e-5
+
+
+def test_batched_parity_with_oracle_small(ffst):
+    shapes = [(128, 128), (64, 64), (128, 256)]
+    imgs = [inputs.scaled_cartoon(r, c, seed=5 + i) for i, (r, c) in enumerate(shapes)]
+    bp = ffst.BatchPlan(shapes, lanes=2)
+    stacks = bp.forward([torch.from_numpy(x).cuda() for x in imgs])
+    for x, s in zip(imgs, stacks):
+        ref = o.forward(x.astype(np.float64))
+        assert np.linalg.norm(s.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float16"])
+def test_graph_replay_equals_eager(ffst, dtype):
+    shapes, imgs = _batch(8, seed=3)
+    tdt = getattr(torch, dtype)
+    bp = ffst.BatchPlan(shapes, lanes=4)
+    stacks = bp.empty_stacks(tdt)
+    scales = [torch.empty(bp.shape(i)[0], device="cuda") for i in range(len(bp))] if dtype != "float32" else None
+    outs = [torch.empty_like(x) for x in imgs]
+    g = bp.capture(imgs, stacks, outs, what=3, plane_scales=scales)
+    eager = bp.forward(imgs, dtype=tdt, plane_scales=[s.clone() for s in scales] if scales else None)
+    eager_stacks = eager[0] if scales else eager
+    eager_scales = eager[1] if scales else None
+    eager_rec = bp.inverse(eager_stacks, plane_scales=eager_scales)
+    for _ in range(2):  # new inputs written into the captured buffers, replayed twice
+        for x in imgs:
+            x.mul_(0.5)
+        g.launch()
+        torch.cuda.synchronize()
+    eager = bp.forward(imgs, dtype=tdt, plane_scales=eager_scales)
+    eager_stacks = eager[0] if scales else eager
+    eager_rec = bp.inverse(eager_stacks, plane_scales=eager_scales)
+    torch.cuda.synchronize()
+    for i in range(len(bp)):
+        assert torch.equal(stacks[i], eager_stacks[i]), i
+        assert torch.equal(outs[i], eager_rec[i]), i
+    g.close()
+
+
+def test_autotune_round_trip(ffst, tmp_path):
+    cache = tmp_path / "ffst_tune.txt"
+    os.environ["FFST_AUTOTUNE_CACHE"] = str(cache)
+    try:
+        x = torch.from_numpy(inputs.scaled_cartoon(512, 512, seed=1)).cuda()
+        p = ffst.Plan(512, 512)
+        before = p.forward(x).clone()
+        mb = p.autotune(reps=2)
+        assert mb in (16.0, 32.0, 64.0, 96.0, 128.0)
+        assert p.group_mb == mb
+        after = p.forward(x)
+        assert torch.equal(before, after)  # the grouping does not change results
+        text = cache.read_text().strip().splitlines()
+        assert len(text) == 1 and text[0].endswith(" %g" % mb) and " 512 512 4 0 " in text[0]
+        q = ffst.Plan(512, 512)  # picks the cached budget up
+        assert q.group_mb == mb
+    finally:
+        del os.environ["FFST_AUTOTUNE_CACHE"]
