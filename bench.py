@@ -301,6 +301,8 @@ def run_gpu(args):
     e2e_ms = _max_over_ranks(a.elapsed_time(b), world, dev)
     e2e_value = coeffs_per_step * args.steps * world / (e2e_ms / 1e3)
 
+    forms = None if args.no_forms else run_forms(plan, pool, stack, rec, value, args, dev)
+
     if rank != 0:
         return 0
 
@@ -345,11 +347,101 @@ def run_gpu(args):
         "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                         "alg_bytes_per_step": v[2] / args.steps} for k, v in kernels.items() if v[1]},
         "gpu_launches": int(sum(v[1] for v in kernels.values())),
+        "forms": forms,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _time_steps(fn, steps, dev):
+    import torch
+
+    stream = torch.cuda.current_stream(dev)
+    for q in range(3):
+        fn(q)
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for q in range(steps):
+        fn(q)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / steps
+
+
+def run_forms(plan, pool, stack, rec, plain_value, args, dev):
+    """The three forms beside the plain FP32 round trip, each timed like the
+    plain step and with its accuracy measured on the GPU against the plain
+    FP32 path (reconstruction error; coefficient error of low-precision
+    storage against the FP32 stack)."""
+    import torch
+
+    import paper_1202_1773_gb300 as ffst
+    from paper_1202_1773_gb300 import inputs
+
+    steps = max(3, args.steps // 2)
+    eta = plan.num_planes
+    cps = eta * ROWS * COLS
+    out = {}
+    x0 = pool[0]
+    ref = plan.forward(x0).clone()
+    xnorm = float(torch.linalg.norm(x0))
+
+    # adjoint: forward + ffst_adjoint (the backward of the differentiable layer)
+    ms = _time_steps(lambda q: (plan.forward(pool[q % len(pool)], out=stack), plan.adjoint(stack, out=rec)), steps, dev)
+    plan.forward(x0, out=stack)
+    err = float(torch.linalg.norm(plan.adjoint(stack) - x0)) / xnorm
+    out["adjoint"] = {"value": cps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "vs_plain": cps / (ms / 1e3) / plain_value,
+                      "accuracy": {"reconstruction_rel_l2": err}}
+
+    # low-precision stack storage (FP32 arithmetic)
+    for name, dt, tol in (("f16", torch.float16, 2e-3), ("bf16", torch.bfloat16, 1e-2)):
+        lp = torch.empty(plan.shape, dtype=dt, device=dev)
+        sc = torch.empty(eta, device=dev)
+        ms = _time_steps(lambda q: (plan.forward(pool[q % len(pool)], out=lp, plane_scale=sc),
+                                    plan.inverse(lp, plane_scale=sc, out=rec)), steps, dev)
+        plan.forward(x0, out=lp, plane_scale=sc)
+        cerr = 0.0
+        for i in range(eta):  # plane by plane, no full-size temporaries
+            d = lp[i].float() / sc[i] - ref[i]
+            cerr += float((d.double() ** 2).sum())
+        cerr = (cerr / sum(float((ref[i].double() ** 2).sum()) for i in range(eta))) ** 0.5
+        rerr = float(torch.linalg.norm(plan.inverse(lp, plane_scale=sc) - x0)) / xnorm
+        byts = 2.0 * cps * 2 + 8.0 * ROWS * COLS
+        out[name] = {"value": cps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                     "vs_plain": cps / (ms / 1e3) / plain_value, "stack_bytes_saved": cps * 2,
+                     "roofline_step_frac": byts / (ms / 1e3) / 1e9 / _peaks()[0],
+                     "accuracy": {"coeff_rel_l2_vs_f32": cerr, "reconstruction_rel_l2": rerr, "tolerance": tol}}
+        del lp
+
+    # batched: 256 images of uneven sizes, forward + inverse replayed from one CUDA graph
+    del ref
+    n = 256
+    shapes = inputs.batch_sizes(n, seed=2)
+    srcs = {}
+    for (r, c) in sorted(set(shapes)):
+        srcs[(r, c)] = [torch.from_numpy(inputs.scaled_cartoon(r, c, seed=300 + q)).to(dev) for q in range(2)]
+    imgs = [srcs[sh][i % 2] for i, sh in enumerate(shapes)]
+    bp = ffst.BatchPlan(shapes, lanes=4, device=dev)
+    stacks = bp.empty_stacks()
+    outs = [torch.empty(sh, device=dev) for sh in shapes]
+    graph = bp.capture(imgs, stacks, outs, what=3)
+    total = sum(bp.shape(i)[0] * shapes[i][0] * shapes[i][1] for i in range(n))
+    ms = _time_steps(lambda q: graph.launch(), max(2, args.steps // 5), dev)
+    errs = [float(torch.linalg.norm(outs[i] - imgs[i]) / torch.linalg.norm(imgs[i])) for i in range(n)]
+    byts = 2.0 * total * 4 + 8.0 * sum(r * c for r, c in shapes)
+    out["batched"] = {"value": total / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                      "vs_plain": total / (ms / 1e3) / plain_value, "images": n,
+                      "sizes": {f"{r}x{c}": shapes.count((r, c)) for (r, c) in sorted(set(shapes))},
+                      "coeffs_per_step": total, "lanes": 4, "graph": True,
+                      "roofline_step_frac": byts / (ms / 1e3) / 1e9 / _peaks()[0],
+                      "accuracy": {"reconstruction_rel_l2_max": max(errs)}}
+    graph.close()
+    bp.close()
+    return out
 
 
 def main():
@@ -359,6 +451,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the adjoint / f16 / bf16 / batched forms")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
