@@ -42,6 +42,26 @@ METRIC = "fwd+inv shearlet coeffs/s (2048x2048 f32, J=5, eta=125)"
 UNIT = "coeffs/s"
 
 
+def _measured_traffic(kind):
+    """DRAM bytes per launch of a kernel kind from the committed ncu capture
+    (profiles/ffst_2048x2048_j5_dram_traffic.json), or None when the kernel
+    sources changed since that capture."""
+    import glob
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "ffst_2048x2048_j5_dram_traffic.json")) as fh:
+            d = json.load(fh)
+        src = sorted(glob.glob(os.path.join(ROOT, "paper_1202_1773_gb300", "csrc", "*")) +
+                     glob.glob(os.path.join(ROOT, "include", "*.h")))
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
+        if h != d["source_hash"]:
+            return None
+        return d["kernels"][kind]["traffic_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -313,8 +333,8 @@ def run_gpu(args):
     if kbytes > 0 and kn > 0:
         achieved = (kbytes / kn) / ((kms / kn) / 1e3) / 1e9
         roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                "launches": kn, "avg_ms": kms / kn}
+                "frac": achieved / peak, "traffic": _measured_traffic(name), "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": kbytes / kn, "launches": kn, "avg_ms": kms / kn}
     else:
         roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,
                 "traffic": None, "launches": kn, "avg_ms": kms / max(kn, 1),
