@@ -6,6 +6,7 @@
 //   inverse:  S = 0;  rows(0);  [rows(g) | cols(g-1)] for g = 1..G-1;  cols(G-1);  ifft2(S)
 // where [a | b] is one fused launch whose blocks interleave both passes
 // (square images); other sizes run the same passes as separate launches.
+#include <cstdlib>
 #include <cstring>
 
 #include "ffst_kernels.cuh"
@@ -51,6 +52,16 @@ static ffst_status check_storage(int storage, const float* scale, const char* fn
 
 static float2* hbuf(const ffst_plan_s* p, size_t g) { return p->d_H + (g % 2) * p->h_elems; }
 
+// Fused launches for square images unless FFST_FUSE=0 (separate launches of
+// the same passes, e.g. to time them apart).
+static bool use_fused(const ffst_plan_s* p) {
+  static const bool off = [] {
+    const char* e = std::getenv("FFST_FUSE");
+    return e && e[0] == '0';
+  }();
+  return !off && fused_supported(p->M, p->N);
+}
+
 static FwdColsArgs fwd_cols_args(const ffst_plan_s* p, const Group& g, float2* H, float* partials) {
   FwdColsArgs a;
   a.F = p->d_F;
@@ -62,6 +73,7 @@ static FwdColsArgs fwd_cols_args(const ffst_plan_s* p, const Group& g, float2* H
   a.w = p->win;
   a.tw = p->d_tw_cols;
   a.partials = partials ? partials + g.item0 : nullptr;
+  a.gain = 1.0f / (kR2CGain * (float)p->M * (float)p->N);
   return a;
 }
 
@@ -80,7 +92,7 @@ static C2RArgs plane_c2r_args(const ffst_plan_s* p, const Group& g, const float2
   a.dst_plane_stride = plane;
   a.st = storage;
   a.plane_scale = plane_scale;
-  a.scale = 1.0f / (float)plane;
+  a.scale = 1.0f;  // fwd_cols already applied 1/(M N) (and the R2C gain)
   a.tw = p->d_tw_rows;
   a.rtw = p->d_rtw;
   return a;
@@ -153,7 +165,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
                  [&] { return launch_plane_scales(p, p->groups[gi], partials, target, plane_scale, s); });
   };
   const size_t G = p->groups.size();
-  if (fused_supported(p->M, p->N)) {
+  if (use_fused(p)) {
     e = timed(p, kTimeFwdCols, 0.0, s, [&] {
       return launch_fwd_cols(p->M, fwd_cols_args(p, p->groups[0], hbuf(p, 0), partials), p->groups[0].nitems, s);
     });
@@ -203,7 +215,7 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
   cudaError_t e = cudaMemsetAsync(p->d_S, 0, sizeof(float2) * (size_t)p->M * p->Hc, s);
   if (e != cudaSuccess) return cuda_fail(e, "inverse accumulator clear");
   const size_t G = p->groups.size();
-  if (fused_supported(p->M, p->N)) {
+  if (use_fused(p)) {
     {
       const Group& rg = p->groups[0];
       e = timed(p, kTimeInvRows, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
@@ -249,7 +261,7 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
   oa.M = p->M;
   oa.dst = img;
   oa.st = FFST_STORE_F32;
-  oa.scale = 1.0f / (float)plane;
+  oa.scale = 1.0f / (kR2CGain * (float)plane);
   oa.tw = p->d_tw_rows;
   oa.rtw = p->d_rtw;
   e = timed(p, kTimeOutRows, 4.0 * plane, s, [&] { return launch_rows_c2r(Lr, oa, 1, s); });

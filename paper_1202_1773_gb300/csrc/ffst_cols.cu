@@ -142,8 +142,8 @@ cudaError_t launch_plane_scales(const ffst_plan_s* p, const Group& g, const floa
                                 float* plane_scale, cudaStream_t s) {
   const int n = g.p1 - g.p0;
   if (n <= 0) return cudaSuccess;
-  k_plane_scales<<<(n + 127) / 128, 128, 0, s>>>(p->d_planes, g.p0, g.p1, partials, 1.0f / ((float)p->M * p->N),
-                                                 target, plane_scale);
+  // the forward column pass folds 1/(M N) into G, so its partials bound max |c_i| directly
+  k_plane_scales<<<(n + 127) / 128, 128, 0, s>>>(p->d_planes, g.p0, g.p1, partials, 1.0f, target, plane_scale);
   return cudaGetLastError();
 }
 

@@ -125,6 +125,33 @@ __device__ __forceinline__ int spad(int i) {
   return i + (i >> ilog2c(E));
 }
 
+// Register layout <-> team buffer: thread t's element m is x[t + T*m].  When
+// T is a multiple of E the pad term splits, spad(t + T m) = spad(t) +
+// m (T + T/E), so one address serves all E slots.
+template <int E, int T>
+__device__ __forceinline__ void team_store(float2* buf, int t, const float2 (&v)[E]) {
+  if constexpr (T % E == 0) {
+    float2* p = buf + spad<E>(t);
+#pragma unroll
+    for (int m = 0; m < E; ++m) p[m * (T + T / E)] = v[m];
+  } else {
+#pragma unroll
+    for (int m = 0; m < E; ++m) buf[spad<E>(t + T * m)] = v[m];
+  }
+}
+
+template <int E, int T>
+__device__ __forceinline__ void team_load(const float2* buf, int t, float2 (&v)[E]) {
+  if constexpr (T % E == 0) {
+    const float2* p = buf + spad<E>(t);
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = p[m * (T + T / E)];
+  } else {
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = buf[spad<E>(t + T * m)];
+  }
+}
+
 // float2 slots per team buffer for a line of length L with E per thread,
 // rounded so that (stride mod 16) == skew; consecutive team buffers then
 // start on different banks (skew chosen by the kernel's lane layout).
@@ -181,15 +208,18 @@ __device__ __forceinline__ void stockham(float2 (&v)[E], float2* buf, int t, con
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q + B * r] = x[r];
     } else {
-      const int base = (j / Ns) * Ns * R + kk;
+      // Ns is 1 (then base is a multiple of R = E) or a multiple of E, so the
+      // pad term of base + r Ns splits and the R slots sit at fixed offsets
+      static_assert(Ns == 1 ? R == E : Ns % E == 0, "pass start must be 1 (radix E) or a multiple of E");
+      constexpr int kStep = Ns == 1 ? 1 : Ns + Ns / E;
+      float2* dst = buf + spad<E>((j / Ns) * Ns * R + kk);
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[spad<E>(base + r * Ns)] = x[r];
+      for (int r = 0; r < R; ++r) dst[r * kStep] = x[r];
     }
   }
   if constexpr (Ns * R < L) {
     team_sync<SYNC, T>(bar);
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = buf[spad<E>(t + T * m)];
+    team_load<E, T>(buf, t, v);
     team_sync<SYNC, T>(bar);
     stockham<L, E, INV, Ns * R, SYNC>(v, buf, t, tw, bar);
   }

@@ -9,6 +9,8 @@
 //  R2C: Z = FFT_L(z);  X[k] = E[k] + W_N^k O[k] with
 //       E[k] = (Z[k] + conj Z[L-k]) / 2,  O[k] = (Z[k] - conj Z[L-k]) / (2i),
 //       for the kept columns k in [c0, c0 + W) of [0, N/2] (W_N = e^{-2 pi i/N}).
+//       The kernel writes 2 X[k] (kR2CGain): the halving is left to the
+//       consumers, which fold it into a scale they apply anyway.
 //  C2R: Z[k] = (X[k] + conj X[L-k]) + i W_N^{-k} (X[k] - conj X[L-k]),
 //       k in [0, L); z = IFFT_L(Z) holds x[2n] + i x[2n+1] (times N for the
 //       unnormalised inverse).  Columns outside [c0, c0 + W) are zero (the
@@ -52,6 +54,9 @@ __device__ __forceinline__ void store_pair(void* p, long long i, float a, float 
   else
     __stcs(reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(p) + i), __floats2bfloat162_rn(a, b));
 }
+
+// Every half spectrum the row R2C writes is kR2CGain times the DFT.
+constexpr float kR2CGain = 2.0f;
 
 // ---------------------------------------------------------------------------
 // geometry
@@ -112,14 +117,24 @@ __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, 
   const void* src = static_cast<const char*>(a.src) + (long long)by * a.src_plane_stride * stor_bytes(a.st);
   const float us = (a.st != FFST_STORE_F32 && a.plane_scale) ? 1.0f / __ldg(&a.plane_scale[plane]) : 1.0f;
   float2 v[E];
+  const long long rbase = (long long)row * N + 2 * t;
+  if (!act) {
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const float2 x = act ? load_pair(src, (long long)row * N + 2 * (t + T * m), a.st) : make_float2(0.f, 0.f);
-    v[m] = make_float2(x.x * us, x.y * us);
+    for (int m = 0; m < E; ++m) v[m] = make_float2(0.f, 0.f);
+  } else if (a.st == FFST_STORE_F32) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = load_pair(src, rbase + 2 * T * m, FFST_STORE_F32);
+  } else {
+    const int st = a.st;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const float2 x = st == FFST_STORE_F16 ? load_pair(src, rbase + 2 * T * m, FFST_STORE_F16)
+                                            : load_pair(src, rbase + 2 * T * m, FFST_STORE_BF16);
+      v[m] = make_float2(x.x * us, x.y * us);
+    }
   }
   line_fft<L, E, false, RowCfg<L>::SYNC>(v, buf, t, a.tw, 1 + team);
-#pragma unroll
-  for (int m = 0; m < E; ++m) buf[spad<E>(t + T * m)] = v[m];
+  team_store<E, T>(buf, t, v);
   team_sync<RowCfg<L>::SYNC, T>(1 + team);
   if (!act) return;
   int c0 = a.c0, W = a.W, ld = a.ld;
@@ -136,8 +151,8 @@ __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, 
     const int k = c0 + idx;  // 0 .. L
     const float2 zk = buf[spad<E>(mod_l<L>(k))];
     const float2 zn = buf[spad<E>(mod_l<L>(L - k))];
-    const float2 e = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
-    const float2 o = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
+    const float2 e = make_float2(zk.x + zn.x, zk.y - zn.y);  // 2 E[k]
+    const float2 o = make_float2(zk.y + zn.y, zn.x - zk.x);  // 2 O[k]
     const float2 w = __ldg(&a.rtw[k]);
     __stcg(&drow[idx], make_float2(e.x + w.x * o.x - w.y * o.y, e.y + w.x * o.y + w.y * o.x));
   }
@@ -153,7 +168,7 @@ struct C2RArgs {
   long long dst_plane_stride;
   int st;                   // storage code of dst
   const float* plane_scale;  // low-precision storage: multiply by s_i before rounding
-  float scale;               // 1/(M N)
+  float scale;               // output factor (1 when the producer already normalised)
   const float2* tw;
   const float2* rtw;
 };
@@ -191,17 +206,28 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
     }
     const float2 e = make_float2(xa.x + xb.x, xa.y - xb.y);  // X[k] + conj X[L-k]
     const float2 d = make_float2(xa.x - xb.x, xa.y + xb.y);  // X[k] - conj X[L-k]
-    float2 w = __ldg(&a.rtw[k]);                             // W_N^k; W_N^{-k} = conj
-    w.x *= s;
-    w.y *= s;
+    const float2 w = __ldg(&a.rtw[k]);                       // W_N^k; W_N^{-k} = conj
     const float2 wd = make_float2(w.x * d.x + w.y * d.y, w.x * d.y - w.y * d.x);
-    v[m] = make_float2(fmaf(e.x, s, -wd.y), fmaf(e.y, s, wd.x));
+    v[m] = make_float2(e.x - wd.y, e.y + wd.x);
+  }
+  if (s != 1.0f) {  // the transform is linear: scale before it, where the values are in registers
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = make_float2(v[m].x * s, v[m].y * s);
   }
   line_fft<L, E, true, RowCfg<L>::SYNC>(v, buf, t, a.tw, 1 + team);
   if (!act) return;
   void* dst = static_cast<char*>(a.dst) + (long long)by * a.dst_plane_stride * stor_bytes(a.st);
+  const long long rbase = (long long)row * N + 2 * t;
+  if (a.st == FFST_STORE_F32) {
 #pragma unroll
-  for (int m = 0; m < E; ++m) store_pair(dst, (long long)row * N + 2 * (t + T * m), v[m].x, v[m].y, a.st);
+    for (int m = 0; m < E; ++m) store_pair(dst, rbase + 2 * T * m, v[m].x, v[m].y, FFST_STORE_F32);
+  } else if (a.st == FFST_STORE_F16) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) store_pair(dst, rbase + 2 * T * m, v[m].x, v[m].y, FFST_STORE_F16);
+  } else {
+#pragma unroll
+    for (int m = 0; m < E; ++m) store_pair(dst, rbase + 2 * T * m, v[m].x, v[m].y, FFST_STORE_BF16);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -245,6 +271,7 @@ struct FwdColsArgs {
   WinParams w;
   const float2* tw;
   float* partials;          // per item sum |G| (low-precision storage), or null
+  float gain;               // G = gain * psi_hat * F (folds the 1/(M N) of the inverse DFT)
 };
 
 // Forward column pass of one plane panel (Sec. 3.1 eq. shearletTransform):
@@ -256,7 +283,8 @@ struct FwdColsArgs {
 // the register layout of the FFT.  With `partials` the block also writes
 // sum |G| over its panel, each column counted once for itself and once for
 // its conjugate partner (columns 0 and N/2 are their own partners); a
-// plane's partials add up to sum_omega |G(omega)| >= M N max_m |c_i(m)|.
+// plane's partials add up to sum_omega |G(omega)| >= max_m |c_i(m)| (G
+// carries the 1/(M N) of the inverse DFT through `gain`).
 template <int L>
 __device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int item, float2* smem) {
   constexpr int E = ColCfg<L>::E, T = ColCfg<L>::T, P = ColCfg<L>::P;
@@ -273,7 +301,7 @@ __device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int item, fl
     const int row = mod_l<L>(rg.x + q);
     const float psi = win_at(a.w, d, row, c);
     float2 g = make_float2(0.f, 0.f);
-    if (psi != 0.0f) g = cscale(a.F[(long long)row * a.Hc + c], psi);
+    if (psi != 0.0f) g = cscale(a.F[(long long)row * a.Hc + c], psi * a.gain);
     buf[spad<E>(row)] = g;
     if (a.partials) mag += sqrtf(g.x * g.x + g.y * g.y);
   }

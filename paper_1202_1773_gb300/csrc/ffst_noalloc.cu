@@ -286,6 +286,7 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
     ca.w = P.win;
     ca.tw = P.d_tw_cols;
     ca.partials = nullptr;
+    ca.gain = 1.0f / (kR2CGain * (float)plane);
     e = launch_fwd_cols(rows, ca, (p1 - p0) * su.ipp, s);
     if (e != cudaSuccess) break;
     C2RArgs ra;
@@ -297,7 +298,7 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
     ra.dst = coeffs + (long long)p0 * plane;
     ra.dst_plane_stride = plane;
     ra.st = FFST_STORE_F32;
-    ra.scale = 1.0f / (float)plane;
+    ra.scale = 1.0f;
     ra.tw = P.d_tw_rows;
     ra.rtw = P.d_rtw;
     e = launch_rows_c2r(cols / 2, ra, p1 - p0, s);
