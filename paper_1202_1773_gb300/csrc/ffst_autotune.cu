@@ -18,7 +18,7 @@
 
 namespace ffst {
 
-static const double kCandidatesMB[] = {16.0, 32.0, 64.0, 96.0, 128.0};
+static const double kCandidatesMB[] = {32.0, 64.0, 96.0, 128.0, 192.0};
 static std::mutex g_cache_mutex;
 
 static std::string cache_path() {

@@ -63,10 +63,12 @@ static cudaError_t cols_fft_L(float2* buf, int width, int ld, bool inverse, cons
 
 template <int L>
 static cudaError_t fwd_cols_L(const FwdColsArgs& a, int nitems, cudaStream_t s) {
-  if (nitems == 0) return cudaSuccess;
+  if (nitems <= 0) return cudaSuccess;
   cudaError_t e = set_smem(k_fwd_cols<L>, ColCfg<L>::SMEM);
   if (e != cudaSuccess) return e;
-  k_fwd_cols<L><<<nitems, kThreads, ColCfg<L>::SMEM, s>>>(a);
+  FwdColsArgs b = a;
+  b.nitems = nitems;
+  k_fwd_cols<L><<<(nitems + kFwdItems - 1) / kFwdItems, kThreads, ColCfg<L>::SMEM, s>>>(b);
   return cudaGetLastError();
 }
 

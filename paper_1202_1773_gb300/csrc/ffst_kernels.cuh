@@ -266,6 +266,7 @@ struct FwdColsArgs {
   int Hc;
   const PlaneDesc* planes;
   const ColItem* items;     // items of this group (index 0 = first item of the group)
+  int nitems;               // items of this group (set by the launchers)
   const int2* rng;
   float2* H;                // base of the group's intermediate
   WinParams w;
@@ -274,62 +275,97 @@ struct FwdColsArgs {
   float gain;               // G = gain * psi_hat * F (folds the 1/(M N) of the inverse DFT)
 };
 
-// Forward column pass of one plane panel (Sec. 3.1 eq. shearletTransform):
+// Forward column items per block.  A block walks kFwdItems consecutive items
+// and fetches the next item's spectrum values during the current FFT; one
+// item per block measured fastest (2 per block: fewer, longer blocks and a
+// longer launch tail, 1.31 -> 1.44 ms forward at 2048x2048 J=5).
+constexpr int kFwdItems = 1;
+
+// Forward column pass of plane panels (Sec. 3.1 eq. shearletTransform):
 // G = psi_hat_i * F on the panel's columns, then the column IFFT; the result
 // goes to the plane's slot of the group intermediate, [M][W_i] starting at
 // column c0_i.  The team of a column evaluates psi only on the column's
 // support rows (one cyclic interval, consecutive rows on consecutive
 // threads), reads F only there, and passes G through its shared buffer into
-// the register layout of the FFT.  With `partials` the block also writes
-// sum |G| over its panel, each column counted once for itself and once for
-// its conjugate partner (columns 0 and N/2 are their own partners); a
+// the register layout of the FFT.  A thread's first support row of the next
+// item (F value and window) is fetched before the current item's FFT, so
+// its load latency hides behind the transform.  With `partials` the block
+// also writes sum |G| per item, each column counted once for itself and once
+// for its conjugate partner (columns 0 and N/2 are their own partners); a
 // plane's partials add up to sum_omega |G(omega)| >= max_m |c_i(m)| (G
 // carries the 1/(M N) of the inverse DFT through `gain`).
 template <int L>
-__device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int item, float2* smem) {
+__device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int blk, float2* smem) {
   constexpr int E = ColCfg<L>::E, T = ColCfg<L>::T, P = ColCfg<L>::P;
   __shared__ float red[kThreads / 32];
   const int t = threadIdx.x / P, cl = threadIdx.x % P;
   float2* buf = smem + cl * ColCfg<L>::BUF;
-  const ColItem it = a.items[item];
-  const PlaneDesc d = a.planes[it.plane];
-  const int c = it.col + cl;
-  const bool act = c < d.c0 + d.W;
-  const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
-  float mag = 0.0f;
-  for (int q = t; q < rg.y; q += T) {
-    const int row = mod_l<L>(rg.x + q);
-    const float psi = win_at(a.w, d, row, c);
-    float2 g = make_float2(0.f, 0.f);
-    if (psi != 0.0f) g = cscale(a.F[(long long)row * a.Hc + c], psi * a.gain);
-    buf[spad<E>(row)] = g;
-    if (a.partials) mag += sqrtf(g.x * g.x + g.y * g.y);
-  }
-  __syncthreads();
-  float2 v[E];
+  const int i0 = blk * kFwdItems;
+  const int i1 = i0 + kFwdItems < a.nitems ? i0 + kFwdItems : a.nitems;
+  // this thread's first support row of item i: F value and window
+  auto prefetch = [&](int i, float2& f, float& psi) {
+    const ColItem it = a.items[i];
+    const PlaneDesc d = a.planes[it.plane];
+    const int c = it.col + cl;
+    const int2 rg = c < d.c0 + d.W ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
+    f = make_float2(0.f, 0.f);
+    psi = 0.0f;
+    if (t < rg.y) {
+      const int row = mod_l<L>(rg.x + t);
+      f = a.F[(long long)row * a.Hc + c];
+      psi = win_at(a.w, d, row, c);
+    }
+  };
+  float2 f0;
+  float psi0;
+  if (i0 < i1) prefetch(i0, f0, psi0);
+  for (int item = i0; item < i1; ++item) {
+    const ColItem it = a.items[item];
+    const PlaneDesc d = a.planes[it.plane];
+    const int c = it.col + cl;
+    const bool act = c < d.c0 + d.W;
+    const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
+    float mag = 0.0f;
+    if (t < rg.y) {
+      const float2 g = cscale(f0, psi0 * a.gain);
+      buf[spad<E>(mod_l<L>(rg.x + t))] = g;
+      if (a.partials) mag += sqrtf(g.x * g.x + g.y * g.y);
+    }
+    for (int q = t + T; q < rg.y; q += T) {
+      const int row = mod_l<L>(rg.x + q);
+      const float psi = win_at(a.w, d, row, c);
+      float2 g = make_float2(0.f, 0.f);
+      if (psi != 0.0f) g = cscale(a.F[(long long)row * a.Hc + c], psi * a.gain);
+      buf[spad<E>(row)] = g;
+      if (a.partials) mag += sqrtf(g.x * g.x + g.y * g.y);
+    }
+    __syncthreads();
+    float2 v[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int row = t + T * m;
-    v[m] = in_range<L>(row, rg) ? buf[spad<E>(row)] : make_float2(0.f, 0.f);
-  }
-  if (a.partials) {
-    const bool self_partner = (c == 0) || (2 * c == a.w.N);
-    mag *= self_partner ? 1.0f : 2.0f;
+    for (int m = 0; m < E; ++m) {
+      const int row = t + T * m;
+      v[m] = in_range<L>(row, rg) ? buf[spad<E>(row)] : make_float2(0.f, 0.f);
+    }
+    if (a.partials) {
+      const bool self_partner = (c == 0) || (2 * c == a.w.N);
+      mag *= self_partner ? 1.0f : 2.0f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mag += __shfl_xor_sync(0xffffffffu, mag, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mag;
-  }
-  __syncthreads();  // buf reads done (and red written) before the FFT reuses buf
-  if (a.partials && threadIdx.x == 0) {
-    float sum = 0.0f;
-    for (int q = 0; q < kThreads / 32; ++q) sum += red[q];
-    a.partials[item] = sum;
-  }
-  line_fft<L, E, true, kSyncBlock>(v, buf, t, a.tw);
-  if (act) {
-    float2* out = a.H + d.off + (c - d.c0);
+      for (int o = 16; o > 0; o >>= 1) mag += __shfl_xor_sync(0xffffffffu, mag, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mag;
+    }
+    __syncthreads();  // buf reads done (and red written) before the FFT reuses buf
+    if (a.partials && threadIdx.x == 0) {
+      float sum = 0.0f;
+      for (int q = 0; q < kThreads / 32; ++q) sum += red[q];
+      a.partials[item] = sum;
+    }
+    if (item + 1 < i1) prefetch(item + 1, f0, psi0);
+    line_fft<L, E, true, kSyncBlock>(v, buf, t, a.tw);  // ends with a barrier after its last buf read
+    if (act) {
+      float2* out = a.H + d.off + (c - d.c0);
 #pragma unroll
-    for (int m = 0; m < E; ++m) __stcg(&out[(long long)(t + T * m) * d.W], v[m]);
+      for (int m = 0; m < E; ++m) __stcg(&out[(long long)(t + T * m) * d.W], v[m]);
+    }
   }
 }
 
@@ -350,6 +386,11 @@ struct InvColsArgs {
 // rows (one cyclic interval, walked by consecutive threads through the
 // team's shared buffer).  Each block owns its columns and visits planes in
 // index order, so the sums are deterministic.
+//
+// Software pipeline: the next plane's column loads are issued as soon as
+// the current spectrum is parked in shared memory, so they fly during the
+// accumulation; a thread's first accumulator element and its window value
+// are fetched before the FFT, while the plane's own loads are in flight.
 template <int L>
 __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, float2* smem) {
   constexpr int E = ColCfg<L>::E, T = ColCfg<L>::T, P = ColCfg<L>::P;
@@ -357,23 +398,51 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
   float2* buf = smem + cl * ColCfg<L>::BUF;
   const int cbase = bx * P;
   const int c = cbase + cl;
-  for (int p = a.p0; p < a.p1; ++p) {
-    const PlaneDesc d = a.planes[p];
-    if (d.W == 0 || d.c0 >= cbase + P || d.c0 + d.W <= cbase) continue;  // uniform over the block
-    const bool act = c >= d.c0 && c < d.c0 + d.W;
-    const float2* in = a.H + d.off + (c - d.c0);
-    float2 v[E];
+  // next plane at or after p whose support meets the panel (uniform over the block)
+  auto next_plane = [&](int p) {
+    for (; p < a.p1; ++p) {
+      const int c0 = a.planes[p].c0, W = a.planes[p].W;
+      if (W != 0 && c0 < cbase + P && c0 + W > cbase) break;
+    }
+    return p;
+  };
+  auto load_cols = [&](int p, float2 (&v)[E]) {
+    const int c0 = a.planes[p].c0, W = a.planes[p].W;
+    const bool act = c >= c0 && c < c0 + W;
+    const float2* in = a.H + a.planes[p].off + (c - c0);
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = act ? __ldcg(&in[(long long)(t + T * m) * d.W]) : make_float2(0.f, 0.f);
+    for (int m = 0; m < E; ++m) v[m] = act ? __ldcg(&in[(long long)(t + T * m) * W]) : make_float2(0.f, 0.f);
+  };
+  int p = next_plane(a.p0);
+  float2 v[E];
+  if (p < a.p1) load_cols(p, v);
+  while (p < a.p1) {
+    const PlaneDesc d = a.planes[p];
+    const bool act = c >= d.c0 && c < d.c0 + d.W;
     const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
+    // first support row of this thread: accumulator value and window, ahead of the FFT
+    const bool first = t < rg.y;
+    const int row0 = mod_l<L>(rg.x + t);
+    float2 s0 = make_float2(0.f, 0.f);
+    float psi0 = 0.0f;
+    if (first) {
+      s0 = a.S[(long long)row0 * a.Hc + c];
+      psi0 = win_at(a.w, d, row0, c);
+    }
     line_fft<L, E, false, kSyncBlock>(v, buf, t, a.tw);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int row = t + T * m;
       if (in_range<L>(row, rg)) buf[spad<E>(row)] = v[m];
     }
+    const int pn = next_plane(p + 1);
+    if (pn < a.p1) load_cols(pn, v);
     __syncthreads();
-    for (int q = t; q < rg.y; q += T) {
+    if (first) {
+      const float2 x = buf[spad<E>(row0)];
+      a.S[(long long)row0 * a.Hc + c] = make_float2(fmaf(psi0, x.x, s0.x), fmaf(psi0, x.y, s0.y));
+    }
+    for (int q = t + T; q < rg.y; q += T) {
       const int row = mod_l<L>(rg.x + q);
       const float psi = win_at(a.w, d, row, c);
       const float2 x = buf[spad<E>(row)];
@@ -381,21 +450,18 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
       const float2 old = *sp;
       *sp = make_float2(fmaf(psi, x.x, old.x), fmaf(psi, x.y, old.y));
     }
-    __syncthreads();  // buf reads done before the next plane's FFT
+    __syncthreads();  // buf reads and S writes done before the next plane
+    p = pn;
   }
 }
 
-// Block b of a launch that interleaves nc column blocks among nr row blocks
-// in proportion: returns true for a column block with index *ci, false for a
-// row block with index *ri.  Every index in [0, nc) and [0, nr) occurs once.
-__device__ __forceinline__ bool split_block(int b, int nc, int nr, int* ci, int* ri) {
-  const long long total = (long long)nc + nr;
-  const int lo = (int)((long long)b * nc / total), hi = (int)((long long)(b + 1) * nc / total);
-  if (hi > lo) {
-    *ci = lo;
+// Block b of a launch whose nc column blocks come first (they run longest).
+__device__ __forceinline__ bool split_cols_first(int b, int nc, int* ci, int* ri) {
+  if (b < nc) {
+    *ci = b;
     return true;
   }
-  *ri = b - lo;
+  *ri = b - nc;
   return false;
 }
 
@@ -411,7 +477,8 @@ cudaError_t launch_inv_cols(int L, const InvColsArgs& a, int npanels, cudaStream
 // Fused launches exist for square images with 256 <= M <= 4096 (fused_supported);
 // other sizes return cudaErrorNotSupported and use the standalone kernels.
 bool fused_supported(int M, int N);
-cudaError_t launch_fwd_fused(int M, const FwdColsArgs& ca, int nc, const C2RArgs& ra, int nplanes, cudaStream_t s);
+cudaError_t launch_fwd_fused(int M, const FwdColsArgs& ca, int nitems, const C2RArgs& ra, int nplanes,
+                             cudaStream_t s);
 cudaError_t launch_inv_fused(int M, const R2CArgs& ra, int nplanes, const InvColsArgs& ca, int nc, cudaStream_t s);
 
 }  // namespace ffst

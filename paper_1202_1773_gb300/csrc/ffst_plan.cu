@@ -209,10 +209,11 @@ static void free_plan(ffst_plan_s* p) {
 // intermediates and the row pass reads them back (two groups in flight,
 // double-buffered); the stack streams past L2 with evict-first hints, so the
 // intermediates mostly stay on chip.  Larger groups mean fewer launches and
-// shorter tails; 96 MB measured best at 2048x2048.  FFST_GROUP_MB overrides
-// the default; ffst_plan_autotune measures the candidates instead.
+// shorter tails; 128 MB measured best at 2048x2048 (with the ramped first
+// and last groups below).  FFST_GROUP_MB overrides the default;
+// ffst_plan_autotune measures the candidates instead.
 double default_group_mb() {
-  double mb = 96.0;
+  double mb = 128.0;
   if (const char* e = std::getenv("FFST_GROUP_MB")) {
     const double v = std::atof(e);
     if (v > 0.0) mb = v;
@@ -220,10 +221,20 @@ double default_group_mb() {
   return mb;
 }
 
+// Size of the first and the last plane group relative to the budget
+// (measured at 2048x2048 J=5, 128 MB: 0.5 -> 2.54 ms fwd+inv, 1 -> 2.61 ms).
+constexpr double kGroupRamp = 0.5;
+
 // (Re)build the plane groups, the forward column work items and the
 // double-buffered intermediate for a group budget of `mb` megabytes.
+// Groups are runs of consecutive planes cut at targets of the cumulative
+// intermediate size (a plane goes to the group its midpoint falls in): the
+// first and the last group aim at kGroupRamp times the budget (they run
+// in launches of their own: the column pass alone before the first fused
+// launch, the row pass alone after the last), the others split the rest
+// evenly into the fewest groups of at most about the budget.
 ffst_status plan_regroup(ffst_plan_s* p, double mb) {
-  const long long budget = (long long)(mb * 1024.0 * 1024.0 / sizeof(float2));
+  const double budget = mb * 1024.0 * 1024.0 / sizeof(float2);
   const int P = cols_per_cta(p->M);
   cudaFree(p->d_items);
   cudaFree(p->d_partials);
@@ -232,17 +243,36 @@ ffst_status plan_regroup(ffst_plan_s* p, double mb) {
   p->d_partials = nullptr;
   p->d_H = nullptr;
   p->groups.clear();
+  auto elems_of = [&](int i) { return (long long)p->M * p->planes[i].W; };
+  double total = 0.0;
+  for (int i = 0; i < p->eta; ++i) total += (double)elems_of(i);
+  std::vector<double> cuts;  // group k holds the planes whose midpoint lies in [cuts[k-1], cuts[k])
+  if (total > budget) {
+    const bool ramp = kGroupRamp < 1.0;
+    const double e = ramp ? std::min(kGroupRamp * budget, total / 3.0) : budget;
+    const double rest = total - (ramp ? 2.0 : 1.0) * e;
+    const int k = std::max(1, (int)std::ceil(rest / budget - 1e-9));
+    cuts.push_back(e);
+    for (int j = 1; j < (ramp ? k + 1 : k); ++j) cuts.push_back(e + rest * j / k);
+  }
   std::vector<ColItem> items;
   Group g{0, 0, 0, 0, 0};
   long long maxg = 0;
+  double acc = 0.0;
+  size_t gk = 0;  // group index of the open group
   for (int i = 0; i < p->eta; ++i) {
-    const long long el = (long long)p->M * p->planes[i].W;
-    if (g.p1 > g.p0 && g.elems + el > budget) {
+    const long long el = elems_of(i);
+    const double mid = acc + 0.5 * (double)el;
+    acc += (double)el;
+    size_t k = 0;
+    while (k < cuts.size() && cuts[k] <= mid) ++k;
+    if (g.p1 > g.p0 && k != gk) {
       g.nitems = (int)items.size() - g.item0;
       p->groups.push_back(g);
       maxg = std::max(maxg, g.elems);
       g = Group{i, i, 0, (int)items.size(), 0};
     }
+    gk = k;
     p->planes[i].off = g.elems;
     p->planes[i].item0 = (int)items.size();
     for (int c = p->planes[i].c0; c < p->planes[i].c0 + p->planes[i].W; c += P) items.push_back(ColItem{i, c});
