@@ -67,8 +67,11 @@ __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c
 #ifndef FFST_ROW_E_LONG
 #define FFST_ROW_E_LONG 16
 #endif
+#ifndef FFST_THREADS
+#define FFST_THREADS 256
+#endif
 #ifndef FFST_MIN_BLOCKS
-#define FFST_MIN_BLOCKS 4
+#define FFST_MIN_BLOCKS (1024 / FFST_THREADS)
 #endif
 __host__ __device__ constexpr bool is_pow2c(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
@@ -109,9 +112,9 @@ __host__ __device__ constexpr bool supported_line(int L) {
          L == 768;
 }
 
-// Every transform kernel runs 256-thread blocks, so a row-pass block and a
-// column-pass block can share one fused launch.
-constexpr int kThreads = 256;
+// Every transform kernel runs blocks of kThreads threads, so a row-pass block
+// and a column-pass block can share one fused launch.
+constexpr int kThreads = FFST_THREADS;
 
 // Entry idx of the pass twiddle table of a line (L, E) (see ffst_fft.cuh):
 // pass with sub-transform length Ns and radix R = min(E, L/Ns) owns indices

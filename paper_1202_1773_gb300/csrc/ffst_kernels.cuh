@@ -194,22 +194,26 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
   float s = a.scale;
   if (a.st != FFST_STORE_F32 && a.plane_scale) s *= __ldg(&a.plane_scale[plane]);
   float2 v[E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
+  // W_N^k for k = t + T m is W_N^t W_{2E}^m: one table entry per thread and
+  // a compile-time root per element (keeps the loads off the L1 pipe;
+  // forward 1.25 -> 1.22 ms at 2048x2048 J=5)
+  const float2 wt = __ldg(&a.rtw[t]);
+  static_for<0, E>([&](auto mc) {
+    constexpr int m = decltype(mc)::value;
     const int k = t + T * m;
     const int ia = k - c0, ib = L - k - c0;
     float2 xa = (act && (unsigned)ia < (unsigned)W) ? __ldcg(&srow[ia]) : make_float2(0.f, 0.f);
     float2 xb = (act && (unsigned)ib < (unsigned)W) ? __ldcg(&srow[ib]) : make_float2(0.f, 0.f);
-    if (k == 0) {  // X[0] and X[N/2]: Hermitian part is real
+    if (m == 0 && t == 0) {  // X[0] and X[N/2]: Hermitian part is real
       xa.y = 0.f;
       xb.y = 0.f;
     }
     const float2 e = make_float2(xa.x + xb.x, xa.y - xb.y);  // X[k] + conj X[L-k]
-    const float2 d = make_float2(xa.x - xb.x, xa.y + xb.y);  // X[k] - conj X[L-k]
-    const float2 w = __ldg(&a.rtw[k]);                       // W_N^k; W_N^{-k} = conj
-    const float2 wd = make_float2(w.x * d.x + w.y * d.y, w.x * d.y - w.y * d.x);
+    // X[k] - conj X[L-k], times conj(W_N^k) = conj(W_N^t) conj(W_{2E}^m)
+    const float2 d = twiddle_c<2 * E, m, true>(make_float2(xa.x - xb.x, xa.y + xb.y));
+    const float2 wd = make_float2(wt.x * d.x + wt.y * d.y, wt.x * d.y - wt.y * d.x);
     v[m] = make_float2(e.x - wd.y, e.y + wd.x);
-  }
+  });
   if (s != 1.0f) {  // the transform is linear: scale before it, where the values are in registers
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = make_float2(v[m].x * s, v[m].y * s);
