@@ -151,8 +151,10 @@ ffst_status ffst_forward_noalloc(int rows, int cols, int scales, const float* im
 /*
  * Autotune a plan's launch configuration for coefficient storage `storage`:
  * times `reps` forward + inverse round trips (after one warm-up) for each
- * candidate plane-group budget (16, 32, 64, 96, 128 MB of column-pass
- * intermediates per fused launch) and keeps the fastest.  Allocates a
+ * candidate plane-group budget (32, 64, 96, 128, 192 MB of column-pass
+ * intermediates per fused launch) and keeps the fastest.  The budget only
+ * matters for grouped launches (schedule mode 0, or sizes without a
+ * persistent schedule).  Allocates a
  * temporary image and coefficient stack of the plan's size (eta*rows*cols
  * elements) and synchronises the device.  When the environment variable
  * FFST_AUTOTUNE_CACHE names a file, the choice is appended to it and later
@@ -163,6 +165,42 @@ ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int reps, double* 
 
 /* The plane-group budget (MB) the plan currently uses. */
 ffst_status ffst_plan_group_mb(ffst_plan_t plan, double* mb);
+
+/*
+ * Schedule of the per-plane passes (implementation choice, no counterpart in
+ * the paper; results are bitwise identical in modes 0 and 1).
+ *   mode 0 (default): grouped launches, one per plane group and pass pair.
+ *   mode 1: persistent schedule, for square images with 256 <= rows <= 4096
+ *           (other sizes keep mode 0): each forward or inverse runs all
+ *           plane passes in one launch whose blocks take column and row tasks
+ *           from a queue built at plan time, with per-plane counters for the
+ *           dependencies and the column intermediates in a ring buffer of
+ *           FFST_RING_MB megabytes (default 256), allocated when mode 1 or 2
+ *           is first selected.  Measured slower than mode 0 at 2048x2048
+ *           (3.3 vs 2.5 ms per forward + inverse).
+ *   mode 2: test mode: the persistent forward's first task waits on a
+ *           counter that nothing increments, so the bounded wait runs out
+ *           (about a second), the launch stops early and ffst_plan_check
+ *           returns FFST_ERR_TIMEOUT; the stack is then unspecified.
+ * ffst_plan_set_schedule returns FFST_ERR_INVALID_ARG for other modes.
+ * ffst_plan_get_schedule stores the mode in effect (0 when the plan has no
+ * persistent schedule).
+ */
+ffst_status ffst_plan_set_schedule(ffst_plan_t plan, int mode);
+ffst_status ffst_plan_get_schedule(ffst_plan_t plan, int* mode);
+
+/* Shape of the persistent schedule (zeros until it is built): resident
+ * blocks per launch, tasks in the forward and inverse queues, ring size in
+ * MB.  Any output pointer may be NULL. */
+ffst_status ffst_plan_schedule_info(ffst_plan_t plan, int* blocks, int* fwd_tasks, int* inv_tasks, double* ring_mb);
+
+/*
+ * Synchronise `stream` and report whether a bounded device-side wait of the
+ * persistent schedule ran out since the last check (FFST_ERR_TIMEOUT; the
+ * flag is then cleared).  Waits only run out in test mode 2 or on an
+ * internal error; the CUDA context stays usable either way.
+ */
+ffst_status ffst_plan_check(ffst_plan_t plan, void* stream);
 
 /*
  * Batches of images of uneven sizes.  ffst_plan_batched builds one plan per

@@ -39,7 +39,11 @@ from ._lib import (  # noqa: F401
     ffst_inverse_batched,
     ffst_plan_autotune,
     ffst_plan_batched,
+    ffst_plan_check,
+    ffst_plan_get_schedule,
     ffst_plan_group_mb,
+    ffst_plan_schedule_info,
+    ffst_plan_set_schedule,
     ffst_forward,
     ffst_forward_noalloc,
     ffst_inverse,
@@ -175,6 +179,23 @@ class Plan:
     @property
     def group_mb(self) -> float:
         return ffst_plan_group_mb(self.handle)
+
+    @property
+    def schedule(self) -> int:
+        """Schedule of the plane passes in effect (ffst_plan_set_schedule): 1 persistent, 0 grouped."""
+        return ffst_plan_get_schedule(self.handle)
+
+    @schedule.setter
+    def schedule(self, mode: int):
+        ffst_plan_set_schedule(self.handle, mode)
+
+    def schedule_info(self) -> dict:
+        """Resident blocks, forward/inverse task counts and ring size of the persistent schedule."""
+        return ffst_plan_schedule_info(self.handle)
+
+    def check(self) -> int:
+        """Synchronise the plan's stream; FFST_ERR_TIMEOUT if a bounded device wait ran out, else 0."""
+        return ffst_plan_check(self.handle, self._stream())
 
     # -- timing ---------------------------------------------------------------
     def timing(self, enable: bool):

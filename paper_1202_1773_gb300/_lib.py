@@ -40,6 +40,11 @@ SIGNATURES = [
     ("ffst_forward_noalloc", _I, [_I, _I, _I, _VP, _VP, _VP]),
     ("ffst_plan_autotune", _I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_double)]),
     ("ffst_plan_group_mb", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    ("ffst_plan_set_schedule", _I, [_VP, _I]),
+    ("ffst_plan_get_schedule", _I, [_VP, ctypes.POINTER(_I)]),
+    ("ffst_plan_check", _I, [_VP, _VP]),
+    ("ffst_plan_schedule_info", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                     ctypes.POINTER(ctypes.c_double)]),
     ("ffst_plan_batched", _I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _I,
                                ctypes.POINTER(_VP)]),
     ("ffst_batch_info", _I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -170,6 +175,28 @@ def ffst_plan_group_mb(plan: int) -> float:
     mb = ctypes.c_double()
     _check("ffst_plan_group_mb", lib().ffst_plan_group_mb(plan, ctypes.byref(mb)))
     return mb.value
+
+
+def ffst_plan_set_schedule(plan: int, mode: int):
+    _check("ffst_plan_set_schedule", lib().ffst_plan_set_schedule(plan, int(mode)))
+
+
+def ffst_plan_get_schedule(plan: int) -> int:
+    mode = _I()
+    _check("ffst_plan_get_schedule", lib().ffst_plan_get_schedule(plan, ctypes.byref(mode)))
+    return mode.value
+
+
+def ffst_plan_check(plan: int, stream: int = 0) -> int:
+    """Status of the bounded device-side waits since the last check (0 = FFST_OK); raises nothing."""
+    return int(lib().ffst_plan_check(plan, stream))
+
+
+def ffst_plan_schedule_info(plan: int) -> dict:
+    b, f, i, mb = _I(), _I(), _I(), ctypes.c_double()
+    _check("ffst_plan_schedule_info", lib().ffst_plan_schedule_info(plan, ctypes.byref(b), ctypes.byref(f),
+                                                                   ctypes.byref(i), ctypes.byref(mb)))
+    return {"blocks": b.value, "fwd_tasks": f.value, "inv_tasks": i.value, "ring_mb": mb.value}
 
 
 def _ints(vals):

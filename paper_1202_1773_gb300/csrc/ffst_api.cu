@@ -40,7 +40,8 @@ static cudaError_t timed(ffst_plan_s* p, int kind, double bytes, cudaStream_t s,
 
 static const char* kKindNames[kTimeKinds] = {"img_rows_r2c", "img_cols_fft", "fwd_cols",      "fwd_rows_c2r",
                                              "inv_rows_r2c", "inv_cols",     "out_cols_ifft", "out_rows_c2r",
-                                             "fwd_fused",    "inv_fused",    "other"};
+                                             "fwd_fused",    "inv_fused",    "fwd_sched",     "inv_sched",
+                                             "other"};
 
 static ffst_status check_storage(int storage, const float* scale, const char* fn) {
   if (storage != FFST_STORE_F32 && storage != FFST_STORE_F16 && storage != FFST_STORE_BF16)
@@ -61,6 +62,11 @@ static bool use_fused(const ffst_plan_s* p) {
   }();
   return !off && fused_supported(p->M, p->N);
 }
+
+// Persistent schedule when the plan has one and its mode selects it.
+static bool use_sched(const ffst_plan_s* p) { return p->sched.on && p->sched_mode != 0; }
+
+static Group all_planes(const ffst_plan_s* p) { return Group{0, p->eta, 0, 0, p->total_items}; }
 
 static FwdColsArgs fwd_cols_args(const ffst_plan_s* p, const Group& g, float2* H, float* partials) {
   FwdColsArgs a;
@@ -165,7 +171,14 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
                  [&] { return launch_plane_scales(p, p->groups[gi], partials, target, plane_scale, s); });
   };
   const size_t G = p->groups.size();
-  if (use_fused(p)) {
+  if (use_sched(p)) {
+    const Group all = all_planes(p);
+    e = timed(p, kTimeFwdSched, (double)p->eta * plane * esz, s, [&] {
+      return launch_fwd_sched(p, fwd_cols_args(p, all, nullptr, partials),
+                              plane_c2r_args(p, all, nullptr, coeffs, storage, nullptr), target,
+                              partials ? plane_scale : nullptr, s);
+    });
+  } else if (use_fused(p)) {
     e = timed(p, kTimeFwdCols, 0.0, s, [&] {
       return launch_fwd_cols(p->M, fwd_cols_args(p, p->groups[0], hbuf(p, 0), partials), p->groups[0].nitems, s);
     });
@@ -215,7 +228,13 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
   cudaError_t e = cudaMemsetAsync(p->d_S, 0, sizeof(float2) * (size_t)p->M * p->Hc, s);
   if (e != cudaSuccess) return cuda_fail(e, "inverse accumulator clear");
   const size_t G = p->groups.size();
-  if (use_fused(p)) {
+  if (use_sched(p)) {
+    const Group all = all_planes(p);
+    e = timed(p, kTimeInvSched, (double)p->eta * plane * esz, s, [&] {
+      return launch_inv_sched(p, plane_r2c_args(p, all, coeffs, storage, plane_scale, nullptr),
+                              inv_cols_args(p, all, nullptr), s);
+    });
+  } else if (use_fused(p)) {
     {
       const Group& rg = p->groups[0];
       e = timed(p, kTimeInvRows, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
@@ -303,6 +322,36 @@ extern "C" ffst_status ffst_adjoint(ffst_plan_t plan, const void* coeffs, int st
   ffst_status st = check_storage(storage, plane_scale, "ffst_adjoint");
   if (st != FFST_OK) return st;
   return synthesis(plan, coeffs, storage, plane_scale, img, static_cast<cudaStream_t>(stream), false);
+}
+
+extern "C" ffst_status ffst_plan_set_schedule(ffst_plan_t plan, int mode) {
+  if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_schedule: plan is NULL");
+  if (mode < 0 || mode > 2) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_schedule: mode must be 0, 1 or 2");
+  if (mode != 0 && !plan->sched.on && fused_supported(plan->M, plan->N)) {  // built on first use
+    const ffst_status st = sched_build(plan, default_ring_mb());
+    if (st != FFST_OK) return st;
+  }
+  plan->sched_mode = mode;
+  return FFST_OK;
+}
+
+extern "C" ffst_status ffst_plan_get_schedule(ffst_plan_t plan, int* mode) {
+  if (!plan || !mode) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_get_schedule: NULL argument");
+  *mode = use_sched(plan) ? plan->sched_mode : 0;
+  return FFST_OK;
+}
+
+extern "C" ffst_status ffst_plan_check(ffst_plan_t plan, void* stream) {
+  if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_check: plan is NULL");
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "ffst_plan_check");
+  if (!plan->sched.d_err) return FFST_OK;
+  int err = 0;
+  e = cudaMemcpy(&err, plan->sched.d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && err) e = cudaMemset(plan->sched.d_err, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "ffst_plan_check");
+  if (err) return fail(FFST_ERR_TIMEOUT, "a persistent-schedule wait ran out; the transform output is unspecified");
+  return FFST_OK;
 }
 
 extern "C" ffst_status ffst_timing_enable(ffst_plan_t plan, int enable) {

@@ -120,24 +120,12 @@ cudaError_t launch_inv_cols(int L, const InvColsArgs& a, int npanels, cudaStream
 #undef CALL_
 }
 
-// s_i = 2^floor(log2(target / B_i)), B_i = (1/MN) sum of the plane's partials
-// (summed in item order: deterministic); s_i = 1 for an all-zero plane.
+// Per-plane scales of low-precision storage (plane_scale_of).
 __global__ void k_plane_scales(const PlaneDesc* __restrict__ planes, int p0, int p1,
-                               const float* __restrict__ partials, float inv_mn, float target,
-                               float* __restrict__ plane_scale) {
+                               const float* __restrict__ partials, float target, float* __restrict__ plane_scale) {
   const int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= p1) return;
-  const PlaneDesc d = planes[p];
-  float sum = 0.0f;
-  for (int q = 0; q < d.nitems; ++q) sum += partials[d.item0 + q];
-  const float B = sum * inv_mn;
-  float s = 1.0f;
-  if (B > 0.0f && isfinite(B)) {
-    int e = (int)floorf(log2f(target / B));
-    e = e < -100 ? -100 : (e > 100 ? 100 : e);
-    s = ldexpf(1.0f, e);
-  }
-  plane_scale[p] = s;
+  plane_scale[p] = plane_scale_of(partials, planes[p].item0, planes[p].nitems, target);
 }
 
 cudaError_t launch_plane_scales(const ffst_plan_s* p, const Group& g, const float* partials, float target,
@@ -145,7 +133,7 @@ cudaError_t launch_plane_scales(const ffst_plan_s* p, const Group& g, const floa
   const int n = g.p1 - g.p0;
   if (n <= 0) return cudaSuccess;
   // the forward column pass folds 1/(M N) into G, so its partials bound max |c_i| directly
-  k_plane_scales<<<(n + 127) / 128, 128, 0, s>>>(p->d_planes, g.p0, g.p1, partials, 1.0f, target, plane_scale);
+  k_plane_scales<<<(n + 127) / 128, 128, 0, s>>>(p->d_planes, g.p0, g.p1, partials, target, plane_scale);
   return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_fwd_fused(FwdCols
   extern __shared__ float2 smem[];
   int ci = 0, ri = 0;
   if (split_cols_first(blockIdx.x, nc, &ci, &ri)) fwd_cols_body<M>(ca, ci, smem);
-  else rows_c2r_body<M / 2>(ra, ri % rbx, ri / rbx, smem);
+  else rows_c2r_body<M / 2>(ra, ri % rbx, ri / rbx, smem, c2r_plane_factor(ra, ri / rbx));
 }
 
 template <int M>

@@ -184,6 +184,8 @@ enum TimingKind : int {
   kTimeOutRows,       // final row C2R to the image
   kTimeFwdFused,      // forward: column pass of group g fused with row pass of group g-1
   kTimeInvFused,      // inverse: row pass of group g fused with column pass of group g-1
+  kTimeFwdSched,      // forward: all plane passes in one persistent launch
+  kTimeInvSched,      // inverse: all plane passes in one persistent launch
   kTimeOther,         // spectra export, plane scales
   kTimeKinds
 };
@@ -202,6 +204,34 @@ struct Timer {
   double total_ms[kTimeKinds] = {0};
   long long launches[kTimeKinds] = {0};
   double bytes[kTimeKinds] = {0};
+};
+
+}  // namespace ffst
+
+namespace ffst {
+
+// Persistent schedule of the plane passes (square sizes, ffst_sched.cu).
+// One launch per direction walks an ordered task queue; per-plane counters
+// carry the dependencies (rows of a plane after its columns, reuse of the
+// intermediate ring after its readers).
+struct Sched {
+  bool on = false;
+  double ring_mb = 0.0;
+  float2* d_ring = nullptr;             // intermediate ring
+  long long ring_elems = 0;
+  PlaneDesc* d_planes = nullptr;        // descriptors with ring offsets
+  int4* d_fwd = nullptr;                // forward queue
+  int n_fwd = 0;
+  int4* d_inv = nullptr;                // inverse queue
+  int n_inv = 0;
+  int4* d_pdep = nullptr;               // per plane: ring predecessors [x, y], their batches [z, w]
+  int2* d_batch = nullptr;              // per inverse batch: planes [x, y)
+  int* d_batch_tasks = nullptr;         // per inverse batch: column tasks
+  int* d_ctl = nullptr;                 // per launch counters (zeroed before each launch)
+  int ctl_ints = 0;
+  int off_cols = 0, off_rows = 0, off_batch = 0, off_panel = 0;  // counter arrays inside d_ctl
+  int* d_err = nullptr;                 // sticky timeout flag (ffst_plan_check reads and clears it)
+  int nbatch = 0, npanels = 0, blocks = 0, rbx = 0;
 };
 
 }  // namespace ffst
@@ -228,6 +258,8 @@ struct ffst_plan_s {
   std::vector<ffst::Group> groups;
   double group_mb = 0.0;                // budget the groups were built for
   ffst::ColItem* d_items = nullptr;
+  ffst::Sched sched;
+  int sched_mode = 0;                   // 0: grouped launches, 1: persistent, 2: persistent with a stuck wait (test)
   ffst::Timer timer;
 };
 
@@ -264,5 +296,10 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
 
 // per-length launch geometry of the column kernels (columns per CTA)
 int cols_per_cta(int L);
+
+// persistent schedule (ffst_sched.cu)
+double default_ring_mb();
+ffst_status sched_build(ffst_plan_s* p, double ring_mb);
+void sched_free(ffst_plan_s* p);
 
 }  // namespace ffst

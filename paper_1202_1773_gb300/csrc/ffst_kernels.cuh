@@ -173,8 +173,31 @@ struct C2RArgs {
   const float2* rtw;
 };
 
+// Factor s_i of plane a.plane0 + by for low-precision storage (1 otherwise),
+// read from the caller's per-plane scales.
+__device__ __forceinline__ float c2r_plane_factor(const C2RArgs& a, int by) {
+  return (a.st != FFST_STORE_F32 && a.plane_scale) ? __ldg(&a.plane_scale[a.plane0 + by]) : 1.0f;
+}
+
+// s_i = 2^floor(log2(target / B_i)), B_i = sum of the plane's forward column
+// partials (item order: deterministic), clamped to 2^+-100; 1 for a zero
+// plane.  The partials are read through L2, so a persistent kernel may call
+// this for partials written by other blocks of the same launch.
+__device__ __forceinline__ float plane_scale_of(const float* partials, int item0, int nitems, float target) {
+  float sum = 0.0f;
+  for (int q = 0; q < nitems; ++q) sum += __ldcg(&partials[item0 + q]);
+  float s = 1.0f;
+  if (sum > 0.0f && isfinite(sum)) {
+    int e = (int)floorf(log2f(target / sum));
+    e = e < -100 ? -100 : (e > 100 ? 100 : e);
+    s = ldexpf(1.0f, e);
+  }
+  return s;
+}
+
+// `ps` is the plane factor s_i multiplied into the output (c2r_plane_factor).
 template <int L>
-__device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, float2* smem) {
+__device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, float2* smem, float ps) {
   constexpr int E = RowCfg<L>::E, T = RowCfg<L>::T, N = 2 * L;
   const int team = threadIdx.x / T, t = threadIdx.x % T;
   float2* buf = smem + team * RowCfg<L>::BUF;
@@ -191,8 +214,7 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
     src = a.src + d.off;
   }
   const float2* srow = src + (long long)row * ld;
-  float s = a.scale;
-  if (a.st != FFST_STORE_F32 && a.plane_scale) s *= __ldg(&a.plane_scale[plane]);
+  const float s = a.scale * ps;
   float2 v[E];
   // W_N^k for k = t + T m is W_N^t W_{2E}^m: one table entry per thread and
   // a compile-time root per element (keeps the loads off the L1 pipe;
@@ -389,7 +411,9 @@ struct InvColsArgs {
 // plane's row spectra, then S += psi_hat_i * (that) on the column's support
 // rows (one cyclic interval, walked by consecutive threads through the
 // team's shared buffer).  Each block owns its columns and visits planes in
-// index order, so the sums are deterministic.
+// index order, so the sums are deterministic.  S is read through L2: in the
+// persistent schedule successive plane batches of a panel may run on
+// different SMs.
 //
 // Software pipeline: the next plane's column loads are issued as soon as
 // the current spectrum is parked in shared memory, so they fly during the
@@ -430,7 +454,7 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
     float2 s0 = make_float2(0.f, 0.f);
     float psi0 = 0.0f;
     if (first) {
-      s0 = a.S[(long long)row0 * a.Hc + c];
+      s0 = __ldcg(&a.S[(long long)row0 * a.Hc + c]);
       psi0 = win_at(a.w, d, row0, c);
     }
     line_fft<L, E, false, kSyncBlock>(v, buf, t, a.tw);
@@ -451,7 +475,7 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
       const float psi = win_at(a.w, d, row, c);
       const float2 x = buf[spad<E>(row)];
       float2* sp = a.S + (long long)row * a.Hc + c;
-      const float2 old = *sp;
+      const float2 old = __ldcg(sp);
       *sp = make_float2(fmaf(psi, x.x, old.x), fmaf(psi, x.y, old.y));
     }
     __syncthreads();  // buf reads and S writes done before the next plane
@@ -481,6 +505,12 @@ cudaError_t launch_inv_cols(int L, const InvColsArgs& a, int npanels, cudaStream
 // Fused launches exist for square images with 256 <= M <= 4096 (fused_supported);
 // other sizes return cudaErrorNotSupported and use the standalone kernels.
 bool fused_supported(int M, int N);
+// Persistent schedule (ffst_sched.cu): one launch for all plane passes of a
+// forward (column items + row C2R) or an inverse (row R2C + column panels).
+// The argument structs are completed inside (ring, descriptors, items).
+cudaError_t launch_fwd_sched(const ffst_plan_s* p, FwdColsArgs ca, C2RArgs ra, float target, float* scale_out,
+                             cudaStream_t st);
+cudaError_t launch_inv_sched(const ffst_plan_s* p, R2CArgs ra, InvColsArgs ca, cudaStream_t st);
 cudaError_t launch_fwd_fused(int M, const FwdColsArgs& ca, int nitems, const C2RArgs& ra, int nplanes,
                              cudaStream_t s);
 cudaError_t launch_inv_fused(int M, const R2CArgs& ra, int nplanes, const InvColsArgs& ca, int nc, cudaStream_t s);

@@ -197,6 +197,7 @@ static void free_plan(ffst_plan_s* p) {
   cudaFree(p->d_H);
   cudaFree(p->d_partials);
   cudaFree(p->d_items);
+  sched_free(p);
   for (auto& r : p->timer.pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

@@ -12,7 +12,7 @@ __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_rows_r2c(R2CArgs 
 template <int L>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_rows_c2r(C2RArgs a) {
   extern __shared__ float2 smem[];
-  rows_c2r_body<L>(a, blockIdx.x, blockIdx.y, smem);
+  rows_c2r_body<L>(a, blockIdx.x, blockIdx.y, smem, c2r_plane_factor(a, blockIdx.y));
 }
 
 template <int L>
