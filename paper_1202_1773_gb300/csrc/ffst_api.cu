@@ -80,6 +80,7 @@ static FwdColsArgs fwd_cols_args(const ffst_plan_s* p, const Group& g, float2* H
   a.tw = p->d_tw_cols;
   a.partials = partials ? partials + g.item0 : nullptr;
   a.gain = 1.0f / (kR2CGain * (float)p->M * (float)p->N);
+  a.tmaps = p->d_tmaps;
   return a;
 }
 
@@ -135,6 +136,8 @@ static InvColsArgs inv_cols_args(const ffst_plan_s* p, const Group& g, const flo
   a.S = p->d_S;
   a.w = p->win;
   a.tw = p->d_tw_cols;
+  a.tmaps = p->d_tmaps;
+  a.err = p->d_err;
   return a;
 }
 
@@ -204,13 +207,14 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
   } else {
     for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
       const Group& gr = p->groups[g];
+      // group g's buffer is hbuf(g) as in the fused schedule (the TMA maps point there)
       e = timed(p, kTimeFwdCols, 0.0, s, [&] {
-        return launch_fwd_cols(p->M, fwd_cols_args(p, gr, hbuf(p, 0), partials), gr.nitems, s);
+        return launch_fwd_cols(p->M, fwd_cols_args(p, gr, hbuf(p, g), partials), gr.nitems, s);
       });
       if (e == cudaSuccess) e = scales(g);
       if (e == cudaSuccess)
         e = timed(p, kTimeFwdRows, (double)(gr.p1 - gr.p0) * plane * esz, s, [&] {
-          return launch_rows_c2r(Lr, plane_c2r_args(p, gr, hbuf(p, 0), coeffs, storage, plane_scale), gr.p1 - gr.p0,
+          return launch_rows_c2r(Lr, plane_c2r_args(p, gr, hbuf(p, g), coeffs, storage, plane_scale), gr.p1 - gr.p0,
                                  s);
         });
     }
@@ -258,12 +262,12 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
     for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
       const Group& gr = p->groups[g];
       e = timed(p, kTimeInvRows, (double)(gr.p1 - gr.p0) * plane * esz, s, [&] {
-        return launch_rows_r2c(Lr, plane_r2c_args(p, gr, coeffs, storage, plane_scale, hbuf(p, 0)), gr.p1 - gr.p0,
+        return launch_rows_r2c(Lr, plane_r2c_args(p, gr, coeffs, storage, plane_scale, hbuf(p, g)), gr.p1 - gr.p0,
                                s);
       });
       if (e == cudaSuccess)
         e = timed(p, kTimeInvCols, 0.0, s,
-                  [&] { return launch_inv_cols(p->M, inv_cols_args(p, gr, hbuf(p, 0)), npanels, s); });
+                  [&] { return launch_inv_cols(p->M, inv_cols_args(p, gr, hbuf(p, g)), npanels, s); });
     }
   }
   if (e != cudaSuccess) return cuda_fail(e, "inverse plane passes");
@@ -345,12 +349,11 @@ extern "C" ffst_status ffst_plan_check(ffst_plan_t plan, void* stream) {
   if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_check: plan is NULL");
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "ffst_plan_check");
-  if (!plan->sched.d_err) return FFST_OK;
   int err = 0;
-  e = cudaMemcpy(&err, plan->sched.d_err, sizeof(int), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && err) e = cudaMemset(plan->sched.d_err, 0, sizeof(int));
+  e = cudaMemcpy(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && err) e = cudaMemset(plan->d_err, 0, sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e, "ffst_plan_check");
-  if (err) return fail(FFST_ERR_TIMEOUT, "a persistent-schedule wait ran out; the transform output is unspecified");
+  if (err) return fail(FFST_ERR_TIMEOUT, "a bounded device-side wait ran out; the transform output is unspecified");
   return FFST_OK;
 }
 

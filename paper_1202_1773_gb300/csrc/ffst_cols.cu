@@ -8,19 +8,19 @@ template <int L, bool INV>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS)
     k_cols_fft(float2* __restrict__ buf, int width, int ld, const float* __restrict__ scale_tab,
                const float2* __restrict__ tw) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   cols_fft_body<L, INV>(buf, width, ld, scale_tab, tw, blockIdx.x, smem);
 }
 
 template <int L>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_fwd_cols(FwdColsArgs a) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   fwd_cols_body<L>(a, blockIdx.x, smem);
 }
 
 template <int L>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_inv_cols(InvColsArgs a) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   inv_cols_body<L>(a, blockIdx.x, smem);
 }
 

@@ -20,7 +20,7 @@ struct FusedCfg {
 
 template <int M>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_fwd_fused(FwdColsArgs ca, int nc, C2RArgs ra, int rbx) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   int ci = 0, ri = 0;
   if (split_cols_first(blockIdx.x, nc, &ci, &ri)) fwd_cols_body<M>(ca, ci, smem);
   else rows_c2r_body<M / 2>(ra, ri % rbx, ri / rbx, smem, c2r_plane_factor(ra, ri / rbx));
@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_fwd_fused(FwdCols
 
 template <int M>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_inv_fused(R2CArgs ra, int rbx, InvColsArgs ca, int nc) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   int ci = 0, ri = 0;
   if (split_cols_first(blockIdx.x, nc, &ci, &ri)) inv_cols_body<M>(ca, ci, smem);
   else rows_r2c_body<M / 2>(ra, ri % rbx, ri / rbx, smem);

@@ -1,6 +1,7 @@
 // Internal declarations of the FFST CUDA library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime's entry-point query)
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -153,8 +154,18 @@ struct PlaneDesc {
   int item0;      // first forward column work item of this plane (global index)
   int nitems;     // number of forward column work items
   int rng_off;    // offset of the plane's per-column row ranges (W entries)
+  int c0al;       // first column of the plane's intermediate slot: c0 rounded down to even
+  int ldw;        // row pitch of the slot: columns c0al .. c0 + W - 1, rounded up to even
   long long off;  // offset of the plane's column-pass intermediate inside its group (float2 units)
 };
+
+// Slot geometry of a plane's intermediate: rows of ldw complex values
+// starting at column c0al, both even, so every row and every 2-column
+// panel starts on a 16-byte boundary (what a TMA tile access needs).
+__host__ __device__ inline void set_slot(PlaneDesc& d) {
+  d.c0al = d.c0 & ~1;
+  d.ldw = d.W ? ((d.c0 + d.W - d.c0al + 1) & ~1) : 0;
+}
 
 // Everything the in-register window generator needs (passed by value).
 struct WinParams {
@@ -230,7 +241,6 @@ struct Sched {
   int* d_ctl = nullptr;                 // per launch counters (zeroed before each launch)
   int ctl_ints = 0;
   int off_cols = 0, off_rows = 0, off_batch = 0, off_panel = 0;  // counter arrays inside d_ctl
-  int* d_err = nullptr;                 // sticky timeout flag (ffst_plan_check reads and clears it)
   int nbatch = 0, npanels = 0, blocks = 0, rbx = 0;
 };
 
@@ -258,6 +268,8 @@ struct ffst_plan_s {
   std::vector<ffst::Group> groups;
   double group_mb = 0.0;                // budget the groups were built for
   ffst::ColItem* d_items = nullptr;
+  CUtensorMap* d_tmaps = nullptr;       // per plane: TMA map of its intermediate slot (or null)
+  int* d_err = nullptr;                 // sticky device error word (bounded waits), read by ffst_plan_check
   ffst::Sched sched;
   int sched_mode = 0;                   // 0: grouped launches, 1: persistent, 2: persistent with a stuck wait (test)
   ffst::Timer timer;
@@ -296,6 +308,10 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
 
 // per-length launch geometry of the column kernels (columns per CTA)
 int cols_per_cta(int L);
+
+// TMA panel maps (ffst_tma_maps.cu), rebuilt whenever the group buffers change
+ffst_status tma_build(ffst_plan_s* p);
+void tma_free(ffst_plan_s* p);
 
 // persistent schedule (ffst_sched.cu)
 double default_ring_mb();

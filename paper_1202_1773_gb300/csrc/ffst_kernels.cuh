@@ -27,6 +27,7 @@
 #pragma once
 
 #include "ffst_fft.cuh"
+#include "ffst_tma.cuh"
 #include "ffst_window.cuh"
 
 namespace ffst {
@@ -139,12 +140,12 @@ __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, 
   if (!act) return;
   int c0 = a.c0, W = a.W, ld = a.ld;
   float2* dst = a.dst;
-  if (a.planes) {
+  if (a.planes) {  // the plane's slot: pitch ldw, column c at c - c0al
     const PlaneDesc d = a.planes[plane];
     c0 = d.c0;
     W = d.W;
-    ld = d.W;
-    dst = a.dst + d.off;
+    ld = d.ldw;
+    dst = a.dst + d.off + (d.c0 - d.c0al);
   }
   float2* drow = dst + (long long)row * ld;
   for (int idx = t; idx < W; idx += T) {
@@ -206,12 +207,12 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
   const bool act = row < a.M;
   int c0 = a.c0, W = a.W, ld = a.ld;
   const float2* src = a.src;
-  if (a.planes) {
+  if (a.planes) {  // the plane's slot: pitch ldw, column c at c - c0al
     const PlaneDesc d = a.planes[plane];
     c0 = d.c0;
     W = d.W;
-    ld = d.W;
-    src = a.src + d.off;
+    ld = d.ldw;
+    src = a.src + d.off + (d.c0 - d.c0al);
   }
   const float2* srow = src + (long long)row * ld;
   const float s = a.scale * ps;
@@ -299,6 +300,7 @@ struct FwdColsArgs {
   const float2* tw;
   float* partials;          // per item sum |G| (low-precision storage), or null
   float gain;               // G = gain * psi_hat * F (folds the 1/(M N) of the inverse DFT)
+  const CUtensorMap* tmaps; // per plane: tensor map of its slot (TMA panel stores), or null
 };
 
 // Forward column items per block.  A block walks kFwdItems consecutive items
@@ -333,7 +335,7 @@ __device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int blk, flo
     const ColItem it = a.items[i];
     const PlaneDesc d = a.planes[it.plane];
     const int c = it.col + cl;
-    const int2 rg = c < d.c0 + d.W ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
+    const int2 rg = (c >= d.c0 && c < d.c0 + d.W) ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
     f = make_float2(0.f, 0.f);
     psi = 0.0f;
     if (t < rg.y) {
@@ -349,7 +351,7 @@ __device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int blk, flo
     const ColItem it = a.items[item];
     const PlaneDesc d = a.planes[it.plane];
     const int c = it.col + cl;
-    const bool act = c < d.c0 + d.W;
+    const bool act = c >= d.c0 && c < d.c0 + d.W;
     const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
     float mag = 0.0f;
     if (t < rg.y) {
@@ -387,10 +389,20 @@ __device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int blk, flo
     }
     if (item + 1 < i1) prefetch(item + 1, f0, psi0);
     line_fft<L, E, true, kSyncBlock>(v, buf, t, a.tw);  // ends with a barrier after its last buf read
-    if (act) {
-      float2* out = a.H + d.off + (c - d.c0);
+    if (a.tmaps) {
+      // the panel [L][P] through shared memory (aliasing the free FFT
+      // buffers) and one TMA store; columns outside the support store zeros
+      float2* tile = smem;
 #pragma unroll
-      for (int m = 0; m < E; ++m) __stcg(&out[(long long)(t + T * m) * d.W], v[m]);
+      for (int m = 0; m < E; ++m) tile[(t + T * m) * P + cl] = act ? v[m] : make_float2(0.f, 0.f);
+      fence_proxy_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) tma_store_panel(&a.tmaps[it.plane], tile, 2 * (it.col - d.c0al));
+      __syncthreads();  // the copy has read the panel before the buffers are reused
+    } else if (act) {
+      float2* out = a.H + d.off + (c - d.c0al);
+#pragma unroll
+      for (int m = 0; m < E; ++m) __stcg(&out[(long long)(t + T * m) * d.ldw], v[m]);
     }
   }
 }
@@ -404,6 +416,8 @@ struct InvColsArgs {
   float2* S;                // [M][Hc] accumulator (zeroed before the first group)
   WinParams w;
   const float2* tw;
+  const CUtensorMap* tmaps; // per plane: tensor map of its slot (TMA panel loads), or null
+  int* err;                 // sticky error word (a TMA wait that ran out sets bit 2)
 };
 
 // Inverse column pass (Sec. 3.3 eq. inverseShearletTransform): for every plane
@@ -422,10 +436,12 @@ struct InvColsArgs {
 template <int L>
 __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, float2* smem) {
   constexpr int E = ColCfg<L>::E, T = ColCfg<L>::T, P = ColCfg<L>::P;
+  __shared__ uint64_t mbar;  // TMA panel loads
   const int t = threadIdx.x / P, cl = threadIdx.x % P;
   float2* buf = smem + cl * ColCfg<L>::BUF;
   const int cbase = bx * P;
   const int c = cbase + cl;
+  const bool tma = a.tmaps != nullptr;
   // next plane at or after p whose support meets the panel (uniform over the block)
   auto next_plane = [&](int p) {
     for (; p < a.p1; ++p) {
@@ -435,15 +451,29 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
     return p;
   };
   auto load_cols = [&](int p, float2 (&v)[E]) {
-    const int c0 = a.planes[p].c0, W = a.planes[p].W;
+    const int c0 = a.planes[p].c0, W = a.planes[p].W, ldw = a.planes[p].ldw;
     const bool act = c >= c0 && c < c0 + W;
-    const float2* in = a.H + a.planes[p].off + (c - c0);
+    const float2* in = a.H + a.planes[p].off + (c - a.planes[p].c0al);
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = act ? __ldcg(&in[(long long)(t + T * m) * W]) : make_float2(0.f, 0.f);
+    for (int m = 0; m < E; ++m) v[m] = act ? __ldcg(&in[(long long)(t + T * m) * ldw]) : make_float2(0.f, 0.f);
   };
+  // TMA: the panel [L][P] of plane p into shared memory (aliasing the FFT
+  // buffers); x may be negative (leading columns read as zeros)
+  auto issue_panel = [&](int p) {
+    if (threadIdx.x == 0)
+      tma_load_panel(&a.tmaps[p], smem, &mbar, 2 * (cbase - a.planes[p].c0al), (unsigned)(L * P * sizeof(float2)));
+  };
+  if (tma) {
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+  }
+  unsigned phase = 0;
   int p = next_plane(a.p0);
   float2 v[E];
-  if (p < a.p1) load_cols(p, v);
+  if (p < a.p1) {
+    if (tma) issue_panel(p);
+    else load_cols(p, v);
+  }
   while (p < a.p1) {
     const PlaneDesc d = a.planes[p];
     const bool act = c >= d.c0 && c < d.c0 + d.W;
@@ -457,6 +487,13 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
       s0 = __ldcg(&a.S[(long long)row0 * a.Hc + c]);
       psi0 = win_at(a.w, d, row0, c);
     }
+    if (tma) {
+      if (!__syncthreads_and(mbar_wait(&mbar, phase, a.err))) return;
+      phase ^= 1;
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = act ? smem[(t + T * m) * P + cl] : make_float2(0.f, 0.f);
+      __syncthreads();  // panel read before the FFT reuses the buffers
+    }
     line_fft<L, E, false, kSyncBlock>(v, buf, t, a.tw);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -464,7 +501,7 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
       if (in_range<L>(row, rg)) buf[spad<E>(row)] = v[m];
     }
     const int pn = next_plane(p + 1);
-    if (pn < a.p1) load_cols(pn, v);
+    if (!tma && pn < a.p1) load_cols(pn, v);
     __syncthreads();
     if (first) {
       const float2 x = buf[spad<E>(row0)];
@@ -479,6 +516,7 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
       *sp = make_float2(fmaf(psi, x.x, old.x), fmaf(psi, x.y, old.y));
     }
     __syncthreads();  // buf reads and S writes done before the next plane
+    if (tma && pn < a.p1) issue_panel(pn);
     p = pn;
   }
 }

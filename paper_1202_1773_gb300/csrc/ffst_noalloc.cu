@@ -40,6 +40,7 @@ constexpr int kNaMaxScales = 4;
 constexpr int kNaMaxPlanes = (1 << (kNaMaxScales + 2)) - 3;  // 61
 constexpr int kNaGroup = 8;                                  // planes per column/row pass pair
 constexpr long long kNaSpec = (long long)kNaMaxSide * (kNaMaxSide / 2 + 1);  // M x (N/2+1) complex
+constexpr long long kNaSlot = (long long)kNaMaxSide * (kNaMaxSide / 2 + 2);  // one plane's intermediate (even pitch)
 constexpr long long kNaMaxItems = (long long)kNaMaxPlanes * 16;              // <= 16 panels per plane
 constexpr long long kNaTabFloats = 2LL * kNaMaxScales * (kNaMaxSide / 2 + 1) + 2 * (kNaMaxSide / 2 + 1);
 
@@ -47,7 +48,7 @@ constexpr long long kNaTabFloats = 2LL * kNaMaxScales * (kNaMaxSide / 2 + 1) + 2
 constexpr long long align256(long long b) { return (b + 255) / 256 * 256; }
 constexpr long long kOffF = 0;
 constexpr long long kOffH = align256(kOffF + kNaSpec * 8);
-constexpr long long kOffPlanes = align256(kOffH + kNaGroup * kNaSpec * 8);
+constexpr long long kOffPlanes = align256(kOffH + kNaGroup * kNaSlot * 8);
 constexpr long long kOffItems = align256(kOffPlanes + kNaMaxPlanes * (long long)sizeof(PlaneDesc));
 constexpr long long kOffTab = align256(kOffItems + kNaMaxItems * (long long)sizeof(ColItem));
 constexpr long long kOffTwR = align256(kOffTab + kNaTabFloats * 4);            // row pass table, N/2 entries
@@ -160,10 +161,11 @@ __global__ void k_na_setup(NaSetup s) {
     na_plane(i, &d.kappa, &d.j, &d.k);
     d.c0 = 0;
     d.W = s.Hc;
+    set_slot(d);
     d.item0 = i * s.ipp;
     d.nitems = s.ipp;
     d.rng_off = i * s.Hc;
-    d.off = (long long)(i % kNaGroup) * s.M * s.Hc;
+    d.off = (long long)(i % kNaGroup) * s.M * d.ldw;
     s.planes[i] = d;
   }
   for (int q = tid; q < s.eta * s.ipp; q += stride) s.items[q] = ColItem{q / s.ipp, (q % s.ipp) * s.P};
@@ -287,6 +289,7 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
     ca.tw = P.d_tw_cols;
     ca.partials = nullptr;
     ca.gain = 1.0f / (kR2CGain * (float)plane);
+    ca.tmaps = nullptr;
     e = launch_fwd_cols(rows, ca, (p1 - p0) * su.ipp, s);
     if (e != cudaSuccess) break;
     C2RArgs ra;

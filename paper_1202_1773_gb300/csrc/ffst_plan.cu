@@ -197,6 +197,8 @@ static void free_plan(ffst_plan_s* p) {
   cudaFree(p->d_H);
   cudaFree(p->d_partials);
   cudaFree(p->d_items);
+  cudaFree(p->d_err);
+  tma_free(p);
   sched_free(p);
   for (auto& r : p->timer.pending) {
     cudaEventDestroy(r.a);
@@ -244,7 +246,7 @@ ffst_status plan_regroup(ffst_plan_s* p, double mb) {
   p->d_partials = nullptr;
   p->d_H = nullptr;
   p->groups.clear();
-  auto elems_of = [&](int i) { return (long long)p->M * p->planes[i].W; };
+  auto elems_of = [&](int i) { return (long long)p->M * p->planes[i].ldw; };
   double total = 0.0;
   for (int i = 0; i < p->eta; ++i) total += (double)elems_of(i);
   std::vector<double> cuts;  // group k holds the planes whose midpoint lies in [cuts[k-1], cuts[k])
@@ -276,7 +278,7 @@ ffst_status plan_regroup(ffst_plan_s* p, double mb) {
     gk = k;
     p->planes[i].off = g.elems;
     p->planes[i].item0 = (int)items.size();
-    for (int c = p->planes[i].c0; c < p->planes[i].c0 + p->planes[i].W; c += P) items.push_back(ColItem{i, c});
+    for (int c = p->planes[i].c0al; c < p->planes[i].c0 + p->planes[i].W; c += P) items.push_back(ColItem{i, c});
     p->planes[i].nitems = (int)items.size() - p->planes[i].item0;
     g.elems += el;
     g.p1 = i + 1;
@@ -299,7 +301,7 @@ ffst_status plan_regroup(ffst_plan_s* p, double mb) {
   }
   if (p->h_elems > 0 && (e = cudaMalloc(&p->d_H, 2 * (size_t)p->h_elems * sizeof(float2))) != cudaSuccess)
     return cuda_fail(e, "workspace H");
-  return FFST_OK;
+  return tma_build(p);
 }
 
 // Pass twiddle table of a line (L, E) (layout in ffst_fft.cuh), FP64 -> FP32.
@@ -443,6 +445,7 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
         p->planes[i].c0 = mm[2 * i];
         p->planes[i].W = mm[2 * i + 1] - mm[2 * i] + 1;
       }
+      set_slot(p->planes[i]);
       p->planes[i].rng_off = rng_total;
       rng_total += p->planes[i].W;
     }
@@ -465,6 +468,8 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
   // workspace
   const size_t spec = (size_t)rows * p->Hc;
   if ((e = cudaMalloc(&p->d_F, spec * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "workspace F");
+  if ((e = cudaMalloc(&p->d_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(p->d_err, 0, sizeof(int))) != cudaSuccess)
+    return cuda_fail(e, "error word");
   if ((e = cudaMalloc(&p->d_S, spec * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "workspace S");
   if ((e = cudaMalloc(&p->d_invD, spec * sizeof(float))) != cudaSuccess) return cuda_fail(e, "normalisation");
   if ((e = launch_inv_norm(p.get(), 0)) != cudaSuccess) return cuda_fail(e, "ffst_plan normalisation");

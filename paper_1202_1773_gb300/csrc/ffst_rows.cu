@@ -5,13 +5,13 @@ namespace ffst {
 
 template <int L>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_rows_r2c(R2CArgs a) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   rows_r2c_body<L>(a, blockIdx.x, blockIdx.y, smem);
 }
 
 template <int L>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_rows_c2r(C2RArgs a) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   rows_c2r_body<L>(a, blockIdx.x, blockIdx.y, smem, c2r_plane_factor(a, blockIdx.y));
 }
 

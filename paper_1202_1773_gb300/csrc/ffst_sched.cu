@@ -118,7 +118,7 @@ struct TaskCursor {
 template <int M>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS)
     k_fwd_sched(SchedArgs s, FwdColsArgs ca, C2RArgs ra) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   __shared__ int slot, ok;
   __shared__ float pscale;
   TaskCursor cur;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS)
 template <int M>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS)
     k_inv_sched(SchedArgs s, R2CArgs ra, InvColsArgs ca) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem[];
   __shared__ int slot, ok;
   TaskCursor cur;
   cur.start(s);
@@ -277,7 +277,7 @@ static SchedArgs sched_args(const ffst_plan_s* p, bool fwd) {
   s.off_rows = sc.off_rows;
   s.off_batch = sc.off_batch;
   s.off_panel = sc.off_panel;
-  s.err = sc.d_err;
+  s.err = p->d_err;
   s.pdep = sc.d_pdep;
   s.batch = sc.d_batch;
   s.batch_tasks = sc.d_batch_tasks;
@@ -302,6 +302,7 @@ cudaError_t launch_fwd_sched(const ffst_plan_s* p, FwdColsArgs ca, C2RArgs ra, f
   ca.nitems = p->total_items;
   ca.H = sc.d_ring;
   ca.partials = scale_out ? p->d_partials : nullptr;
+  ca.tmaps = nullptr;  // the maps describe the group buffers, not the ring
   ra.plane_scale = nullptr;  // the kernel passes the plane factor itself
   ra.src = sc.d_ring;
   ra.planes = sc.d_planes;
@@ -321,6 +322,7 @@ cudaError_t launch_inv_sched(const ffst_plan_s* p, R2CArgs ra, InvColsArgs ca, c
   ra.plane0 = 0;
   ca.H = sc.d_ring;
   ca.planes = sc.d_planes;
+  ca.tmaps = nullptr;  // the maps describe the group buffers, not the ring
 #define CALL_(MM) inv_sched_M<MM>(sc, s, ra, ca, st)
   FFST_DISPATCH_SCHED(p->M, CALL_)
 #undef CALL_
@@ -354,7 +356,6 @@ void sched_free(ffst_plan_s* p) {
   cudaFree(sc.d_batch);
   cudaFree(sc.d_batch_tasks);
   cudaFree(sc.d_ctl);
-  cudaFree(sc.d_err);
   sc = Sched{};
 }
 
@@ -380,13 +381,13 @@ ffst_status sched_build(ffst_plan_s* p, double ring_mb) {
   // ring slots, in plane order, wrapping to the start when a slot would not fit
   long long ring = (long long)(ring_mb * 1024.0 * 1024.0 / sizeof(float2));
   long long biggest = 0;
-  for (int i = 0; i < eta; ++i) biggest = std::max(biggest, (long long)M * p->planes[i].W);
+  for (int i = 0; i < eta; ++i) biggest = std::max(biggest, (long long)M * p->planes[i].ldw);
   ring = std::max(ring, biggest);
   std::vector<PlaneDesc> rp = p->planes;
   std::vector<long long> lo(eta), hi(eta);
   long long cursor = 0;
   for (int i = 0; i < eta; ++i) {
-    const long long n = (long long)M * rp[i].W;
+    const long long n = (long long)M * rp[i].ldw;
     if (cursor + n > ring) cursor = 0;
     rp[i].off = n ? cursor : 0;
     lo[i] = cursor;
@@ -410,7 +411,7 @@ ffst_status sched_build(ffst_plan_s* p, double ring_mb) {
     long long acc = 0;
     int b0 = 0;
     for (int i = 0; i < eta; ++i) {
-      const long long n = (long long)M * rp[i].W;
+      const long long n = (long long)M * rp[i].ldw;
       if (i > b0 && acc + n > ring / 3) {
         batch.push_back(make_int2(b0, i));
         b0 = i;
@@ -578,8 +579,6 @@ ffst_status sched_build(ffst_plan_s* p, double ring_mb) {
   if (e == cudaSuccess) e = upload(&sc.d_batch, batch);
   if (e == cudaSuccess) e = upload(&sc.d_batch_tasks, batch_tasks);
   if (e == cudaSuccess) e = cudaMalloc(&sc.d_ctl, sizeof(int) * (size_t)sc.ctl_ints);
-  if (e == cudaSuccess) e = cudaMalloc(&sc.d_err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(sc.d_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     sched_free(p);
     return cuda_fail(e, "persistent schedule");
