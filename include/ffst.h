@@ -150,21 +150,22 @@ ffst_status ffst_forward_noalloc(int rows, int cols, int scales, const float* im
 
 /*
  * Autotune a plan's launch configuration for coefficient storage `storage`:
- * times `reps` forward + inverse round trips (after one warm-up) for each
- * candidate plane-group budget (32, 64, 96, 128, 192 MB of column-pass
- * intermediates per fused launch) and keeps the fastest.  The budget only
- * matters for grouped launches (schedule mode 0, or sizes without a
- * persistent schedule).  Allocates a
- * temporary image and coefficient stack of the plan's size (eta*rows*cols
- * elements) and synchronises the device.  When the environment variable
+ * for each candidate plane-group budget (32, 64, 96, 128, 192 MB of
+ * column-pass intermediates per fused launch) times `reps` forwards and
+ * inverses (after one warm-up round trip), the two directions apart, and
+ * keeps the fastest budget for each.  Allocates a temporary image and
+ * coefficient stack of the plan's size (eta*rows*cols elements) and
+ * synchronises the device.  When the environment variable
  * FFST_AUTOTUNE_CACHE names a file, the choice is appended to it and later
  * ffst_plan calls for the same device and shape start from it.  Results do
- * not depend on the budget.  *chosen_mb (may be NULL) receives the choice.
+ * not depend on the budgets.  *fwd_mb and *inv_mb (either may be NULL)
+ * receive the choice.  The budgets only matter for grouped launches
+ * (schedule mode 0, the default).
  */
-ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int reps, double* chosen_mb);
+ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int reps, double* fwd_mb, double* inv_mb);
 
-/* The plane-group budget (MB) the plan currently uses. */
-ffst_status ffst_plan_group_mb(ffst_plan_t plan, double* mb);
+/* The plane-group budgets (MB) of the plan's forward and inverse. */
+ffst_status ffst_plan_group_mb(ffst_plan_t plan, double* fwd_mb, double* inv_mb);
 
 /*
  * Schedule of the per-plane passes (implementation choice, no counterpart in

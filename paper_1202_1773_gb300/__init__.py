@@ -170,14 +170,15 @@ class Plan:
         return self._synth(ffst_adjoint, coeffs, plane_scale, out)
 
     # -- tuning ---------------------------------------------------------------
-    def autotune(self, dtype=None, reps: int = 3) -> float:
-        """Measure the plane-group budgets and keep the fastest (see ffst_plan_autotune)."""
+    def autotune(self, dtype=None, reps: int = 3):
+        """Measure the plane-group budgets, keep the fastest per direction; returns (forward MB, inverse MB)."""
         torch = _torch()
         with torch.cuda.device(self.device):
             return ffst_plan_autotune(self.handle, _storage_of(dtype or torch.float32), reps)
 
     @property
-    def group_mb(self) -> float:
+    def group_mb(self):
+        """(forward MB, inverse MB) plane-group budgets."""
         return ffst_plan_group_mb(self.handle)
 
     @property

@@ -38,8 +38,8 @@ SIGNATURES = [
     ("ffst_inverse", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
     ("ffst_adjoint", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
     ("ffst_forward_noalloc", _I, [_I, _I, _I, _VP, _VP, _VP]),
-    ("ffst_plan_autotune", _I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_double)]),
-    ("ffst_plan_group_mb", _I, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    ("ffst_plan_autotune", _I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    ("ffst_plan_group_mb", _I, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("ffst_plan_set_schedule", _I, [_VP, _I]),
     ("ffst_plan_get_schedule", _I, [_VP, ctypes.POINTER(_I)]),
     ("ffst_plan_check", _I, [_VP, _VP]),
@@ -165,16 +165,18 @@ def ffst_forward_noalloc(rows: int, cols: int, scales: int, img, coeffs, stream=
                                                               _ptr(coeffs), stream))
 
 
-def ffst_plan_autotune(plan: int, storage: int = FFST_STORE_F32, reps: int = 3) -> float:
-    mb = ctypes.c_double()
-    _check("ffst_plan_autotune", lib().ffst_plan_autotune(plan, int(storage), int(reps), ctypes.byref(mb)))
-    return mb.value
+def ffst_plan_autotune(plan: int, storage: int = FFST_STORE_F32, reps: int = 3):
+    """(forward MB, inverse MB) chosen."""
+    f, i = ctypes.c_double(), ctypes.c_double()
+    _check("ffst_plan_autotune", lib().ffst_plan_autotune(plan, int(storage), int(reps), ctypes.byref(f), ctypes.byref(i)))
+    return f.value, i.value
 
 
-def ffst_plan_group_mb(plan: int) -> float:
-    mb = ctypes.c_double()
-    _check("ffst_plan_group_mb", lib().ffst_plan_group_mb(plan, ctypes.byref(mb)))
-    return mb.value
+def ffst_plan_group_mb(plan: int):
+    """(forward MB, inverse MB)."""
+    f, i = ctypes.c_double(), ctypes.c_double()
+    _check("ffst_plan_group_mb", lib().ffst_plan_group_mb(plan, ctypes.byref(f), ctypes.byref(i)))
+    return f.value, i.value
 
 
 def ffst_plan_set_schedule(plan: int, mode: int):

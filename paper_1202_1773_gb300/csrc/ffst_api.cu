@@ -116,7 +116,7 @@ static R2CArgs plane_r2c_args(const ffst_plan_s* p, const Group& g, const void* 
   a.plane0 = g.p0;
   a.M = p->M;
   a.dst = H;
-  a.planes = p->d_planes;
+  a.planes = p->d_planes_inv;
   a.c0 = 0;
   a.W = 0;
   a.ld = 0;
@@ -129,14 +129,14 @@ static InvColsArgs inv_cols_args(const ffst_plan_s* p, const Group& g, const flo
   InvColsArgs a;
   a.H = H;
   a.Hc = p->Hc;
-  a.planes = p->d_planes;
+  a.planes = p->d_planes_inv;
   a.p0 = g.p0;
   a.p1 = g.p1;
   a.rng = p->d_rng;
   a.S = p->d_S;
   a.w = p->win;
   a.tw = p->d_tw_cols;
-  a.tmaps = p->d_tmaps;
+  a.tmaps = p->d_tmaps_inv;
   a.err = p->d_err;
   return a;
 }
@@ -231,7 +231,7 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
   const int npanels = (p->Hc + cols_per_cta(p->M) - 1) / cols_per_cta(p->M);
   cudaError_t e = cudaMemsetAsync(p->d_S, 0, sizeof(float2) * (size_t)p->M * p->Hc, s);
   if (e != cudaSuccess) return cuda_fail(e, "inverse accumulator clear");
-  const size_t G = p->groups.size();
+  const size_t G = p->groups_inv.size();
   if (use_sched(p)) {
     const Group all = all_planes(p);
     e = timed(p, kTimeInvSched, (double)p->eta * plane * esz, s, [&] {
@@ -240,15 +240,15 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
     });
   } else if (use_fused(p)) {
     {
-      const Group& rg = p->groups[0];
+      const Group& rg = p->groups_inv[0];
       e = timed(p, kTimeInvRows, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
         return launch_rows_r2c(Lr, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, 0)), rg.p1 - rg.p0,
                                s);
       });
     }
     for (size_t g = 1; g < G && e == cudaSuccess; ++g) {
-      const Group& rg = p->groups[g];
-      const Group& cg = p->groups[g - 1];
+      const Group& rg = p->groups_inv[g];
+      const Group& cg = p->groups_inv[g - 1];
       e = timed(p, kTimeInvFused, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
         return launch_inv_fused(p->M, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, g)), rg.p1 - rg.p0,
                                 inv_cols_args(p, cg, hbuf(p, g - 1)), npanels, s);
@@ -256,11 +256,11 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
     }
     if (e == cudaSuccess)
       e = timed(p, kTimeInvCols, 0.0, s, [&] {
-        return launch_inv_cols(p->M, inv_cols_args(p, p->groups[G - 1], hbuf(p, G - 1)), npanels, s);
+        return launch_inv_cols(p->M, inv_cols_args(p, p->groups_inv[G - 1], hbuf(p, G - 1)), npanels, s);
       });
   } else {
     for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
-      const Group& gr = p->groups[g];
+      const Group& gr = p->groups_inv[g];
       e = timed(p, kTimeInvRows, (double)(gr.p1 - gr.p0) * plane * esz, s, [&] {
         return launch_rows_r2c(Lr, plane_r2c_args(p, gr, coeffs, storage, plane_scale, hbuf(p, g)), gr.p1 - gr.p0,
                                s);

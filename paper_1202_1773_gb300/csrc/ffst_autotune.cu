@@ -3,11 +3,12 @@
 // The knob with the largest measured effect is the plane-group budget (how
 // many planes' column-pass intermediates one fused launch holds): larger
 // groups mean fewer launches and shorter tails, smaller groups keep more of
-// the intermediates in L2.  ffst_plan_autotune times a forward + inverse
-// round trip for each candidate budget on the plan's own shape and keeps the
-// fastest.  With FFST_AUTOTUNE_CACHE set, results are appended to that text
-// file ("<device> <rows> <cols> <scales> <storage> <MB>" per line) and
-// ffst_plan reads them back, so a shape is tuned once per machine.
+// the intermediates in L2.  ffst_plan_autotune times the forward and the
+// inverse of a round trip apart for each candidate budget on the plan's own
+// shape and keeps the fastest for each direction.  With FFST_AUTOTUNE_CACHE
+// set, results are appended to that text file ("<device> <rows> <cols>
+// <scales> <storage> <forward MB> <inverse MB>" per line) and ffst_plan reads
+// them back, so a shape is tuned once per machine.
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
@@ -37,7 +38,7 @@ static std::string plan_key(const ffst_plan_s* p, int storage) {
   return os.str();
 }
 
-bool autotune_lookup(const ffst_plan_s* p, int storage, double* mb) {
+bool autotune_lookup(const ffst_plan_s* p, int storage, double* fwd_mb, double* inv_mb) {
   const std::string path = cache_path();
   if (path.empty()) return false;
   std::lock_guard<std::mutex> lock(g_cache_mutex);
@@ -47,30 +48,30 @@ bool autotune_lookup(const ffst_plan_s* p, int storage, double* mb) {
   std::string line;
   bool found = false;
   while (std::getline(in, line)) {
-    const size_t cut = line.rfind(' ');
-    if (cut == std::string::npos || line.substr(0, cut) != key) continue;
-    const double v = std::atof(line.c_str() + cut + 1);
-    if (v > 0.0) {
-      *mb = v;  // the last entry for a key wins
-      found = true;
-    }
+    if (line.compare(0, key.size() + 1, key + " ") != 0) continue;
+    std::istringstream rest(line.substr(key.size() + 1));
+    double f = 0.0, i = 0.0;
+    if (!(rest >> f >> i) || f <= 0.0 || i <= 0.0) continue;
+    *fwd_mb = f;  // the last entry for a key wins
+    *inv_mb = i;
+    found = true;
   }
   return found;
 }
 
-static void autotune_store(const ffst_plan_s* p, int storage, double mb) {
+static void autotune_store(const ffst_plan_s* p, int storage, double fwd_mb, double inv_mb) {
   const std::string path = cache_path();
   if (path.empty()) return;
   std::lock_guard<std::mutex> lock(g_cache_mutex);
   std::ofstream out(path, std::ios::app);
-  if (out) out << plan_key(p, storage) << ' ' << mb << '\n';
+  if (out) out << plan_key(p, storage) << ' ' << fwd_mb << ' ' << inv_mb << '\n';
 }
 
 }  // namespace ffst
 
 using namespace ffst;
 
-extern "C" ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int reps, double* chosen_mb) {
+extern "C" ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int reps, double* fwd_mb, double* inv_mb) {
   if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_autotune: plan is NULL");
   if (storage < FFST_STORE_F32 || storage > FFST_STORE_BF16)
     return fail(FFST_ERR_INVALID_ARG, "ffst_plan_autotune: unknown storage code");
@@ -83,14 +84,14 @@ extern "C" ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int rep
   float* scale = nullptr;
   void* coeffs = nullptr;
   cudaStream_t s = nullptr;
-  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   auto cleanup = [&] {
     cudaFree(img);
     cudaFree(out);
     cudaFree(scale);
     cudaFree(coeffs);
-    if (a) cudaEventDestroy(a);
-    if (b) cudaEventDestroy(b);
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
     if (s) cudaStreamDestroy(s);
   };
   cudaError_t e;
@@ -102,41 +103,57 @@ extern "C" ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int rep
   }
   cudaMemset(img, 0, plane * 4);
   cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
+  for (auto& x : ev) cudaEventCreate(&x);
   const bool was_timing = p->timer.enabled;
   p->timer.enabled = false;
-  const double before = p->group_mb;
-  double best_mb = before, best_ms = 1e30;
+  // forward and inverse are timed apart: each direction keeps its own best budget
+  double best_f = p->group_mb, best_i = p->group_mb_inv, tf = 1e30, ti = 1e30;
   for (double mb : kCandidatesMB) {
-    if (plan_regroup(p, mb) != FFST_OK) continue;
+    if (plan_regroup(p, mb, mb) != FFST_OK) continue;
     bool ok = true;
+    float f_ms = 0.f, i_ms = 0.f;
     for (int q = 0; q < 1 + reps && ok; ++q) {
-      if (q == 1) cudaEventRecord(a, s);
-      ok = ffst_forward(p, img, coeffs, storage, scale, s) == FFST_OK &&
-           ffst_inverse(p, coeffs, storage, scale, out, s) == FFST_OK;
+      cudaEventRecord(ev[0], s);
+      ok = ffst_forward(p, img, coeffs, storage, scale, s) == FFST_OK;
+      cudaEventRecord(ev[1], s);
+      ok = ok && ffst_inverse(p, coeffs, storage, scale, out, s) == FFST_OK;
+      cudaEventRecord(ev[2], s);
+      if (!ok || cudaEventSynchronize(ev[2]) != cudaSuccess) {
+        ok = false;
+        break;
+      }
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, ev[0], ev[1]);
+      cudaEventElapsedTime(&b, ev[1], ev[2]);
+      if (q > 0) {  // the first round trip is the warm-up
+        f_ms += a;
+        i_ms += b;
+      }
     }
-    cudaEventRecord(b, s);
-    if (!ok || cudaEventSynchronize(b) != cudaSuccess) continue;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best_mb = mb;
+    if (!ok) continue;
+    if (f_ms < tf) {
+      tf = f_ms;
+      best_f = mb;
+    }
+    if (i_ms < ti) {
+      ti = i_ms;
+      best_i = mb;
     }
   }
   p->timer.enabled = was_timing;
-  const ffst_status st = plan_regroup(p, best_mb);
+  const ffst_status st = plan_regroup(p, best_f, best_i);
   cleanup();
   if (st != FFST_OK) return st;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "ffst_plan_autotune");
-  autotune_store(p, storage, best_mb);
-  if (chosen_mb) *chosen_mb = best_mb;
+  autotune_store(p, storage, best_f, best_i);
+  if (fwd_mb) *fwd_mb = best_f;
+  if (inv_mb) *inv_mb = best_i;
   return FFST_OK;
 }
 
-extern "C" ffst_status ffst_plan_group_mb(ffst_plan_t plan, double* mb) {
-  if (!plan || !mb) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_group_mb: NULL argument");
-  *mb = plan->group_mb;
+extern "C" ffst_status ffst_plan_group_mb(ffst_plan_t plan, double* fwd_mb, double* inv_mb) {
+  if (!plan || !fwd_mb || !inv_mb) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_group_mb: NULL argument");
+  *fwd_mb = plan->group_mb;
+  *inv_mb = plan->group_mb_inv;
   return FFST_OK;
 }

@@ -265,10 +265,14 @@ struct ffst_plan_s {
   long long h_elems = 0;
   float* d_partials = nullptr;          // [total items] per-panel sums of |psi F| (low-precision storage)
   int total_items = 0;
-  std::vector<ffst::Group> groups;
-  double group_mb = 0.0;                // budget the groups were built for
+  std::vector<ffst::Group> groups;      // forward plane groups (slot offsets in planes / d_planes)
+  double group_mb = 0.0;                // budget the forward groups were built for
+  std::vector<ffst::Group> groups_inv;  // inverse plane groups
+  double group_mb_inv = 0.0;
+  ffst::PlaneDesc* d_planes_inv = nullptr;  // descriptors with the inverse groups' slot offsets
   ffst::ColItem* d_items = nullptr;
-  CUtensorMap* d_tmaps = nullptr;       // per plane: TMA map of its intermediate slot (or null)
+  CUtensorMap* d_tmaps = nullptr;       // per plane: TMA map of its forward slot (or null)
+  CUtensorMap* d_tmaps_inv = nullptr;   // per plane: TMA map of its inverse slot (or null)
   int* d_err = nullptr;                 // sticky device error word (bounded waits), read by ffst_plan_check
   ffst::Sched sched;
   int sched_mode = 0;                   // 0: grouped launches, 1: persistent, 2: persistent with a stuck wait (test)
@@ -283,9 +287,9 @@ ffst_status fail(ffst_status st, const std::string& msg);
 ffst_status cuda_fail(cudaError_t e, const char* what);
 
 // plan grouping and autotuning (ffst_plan.cu, ffst_autotune.cu)
-double default_group_mb();
-ffst_status plan_regroup(ffst_plan_s* p, double mb);
-bool autotune_lookup(const ffst_plan_s* p, int storage, double* mb);
+void default_group_mb(double* fwd_mb, double* inv_mb);
+ffst_status plan_regroup(ffst_plan_s* p, double fwd_mb, double inv_mb);
+bool autotune_lookup(const ffst_plan_s* p, int storage, double* fwd_mb, double* inv_mb);
 
 // timing helpers
 void timer_begin(ffst_plan_s* p, int kind, cudaStream_t s, double bytes, cudaEvent_t* out_b);
@@ -310,7 +314,7 @@ inline cudaError_t set_smem(K kernel, size_t bytes) {
 int cols_per_cta(int L);
 
 // TMA panel maps (ffst_tma_maps.cu), rebuilt whenever the group buffers change
-ffst_status tma_build(ffst_plan_s* p);
+ffst_status tma_build(ffst_plan_s* p, const std::vector<long long>& off_fwd, const std::vector<long long>& off_inv);
 void tma_free(ffst_plan_s* p);
 
 // persistent schedule (ffst_sched.cu)

@@ -186,6 +186,7 @@ ffst_status cuda_fail(cudaError_t e, const char* what) {
 static void free_plan(ffst_plan_s* p) {
   if (!p) return;
   cudaFree(p->d_planes);
+  cudaFree(p->d_planes_inv);
   cudaFree(p->d_tables);
   cudaFree(p->d_tw_rows);
   cudaFree(p->d_tw_cols);
@@ -208,44 +209,49 @@ static void free_plan(ffst_plan_s* p) {
   delete p;
 }
 
-// Intermediate budget per plane group.  The column pass writes a group's
-// intermediates and the row pass reads them back (two groups in flight,
-// double-buffered); the stack streams past L2 with evict-first hints, so the
-// intermediates mostly stay on chip.  Larger groups mean fewer launches and
-// shorter tails; 128 MB measured best at 2048x2048 (with the ramped first
-// and last groups below).  FFST_GROUP_MB overrides the default;
+// Intermediate budgets per plane group of the forward and of the inverse.
+// The column pass writes a group's intermediates and the row pass reads
+// them back (two groups in flight, double-buffered); the stack streams past
+// L2 with evict-first hints.  Larger groups mean fewer launches and shorter
+// tails, smaller ones keep more of the intermediates in L2; the two
+// directions weigh this differently (2048x2048 J=5, ms: forward 1.07 at
+// 96 MB, 1.12 at 128, 1.16 at 192; inverse 1.17 at 96, 1.10 at 128, 1.07 at
+// 192).  FFST_GROUP_MB sets both, FFST_GROUP_MB_INV the inverse;
 // ffst_plan_autotune measures the candidates instead.
-double default_group_mb() {
-  double mb = 128.0;
+void default_group_mb(double* fwd_mb, double* inv_mb) {
+  double f = 96.0, i = 192.0;
   if (const char* e = std::getenv("FFST_GROUP_MB")) {
     const double v = std::atof(e);
-    if (v > 0.0) mb = v;
+    if (v > 0.0) f = i = v;
   }
-  return mb;
+  if (const char* e = std::getenv("FFST_GROUP_MB_INV")) {
+    const double v = std::atof(e);
+    if (v > 0.0) i = v;
+  }
+  *fwd_mb = f;
+  *inv_mb = i;
 }
 
 // Size of the first and the last plane group relative to the budget
 // (measured at 2048x2048 J=5, 128 MB: 0.5 -> 2.54 ms fwd+inv, 1 -> 2.61 ms).
-constexpr double kGroupRamp = 0.5;
+#ifndef FFST_GROUP_RAMP
+#define FFST_GROUP_RAMP 0.5
+#endif
+constexpr double kGroupRamp = FFST_GROUP_RAMP;
 
-// (Re)build the plane groups, the forward column work items and the
-// double-buffered intermediate for a group budget of `mb` megabytes.
-// Groups are runs of consecutive planes cut at targets of the cumulative
-// intermediate size (a plane goes to the group its midpoint falls in): the
-// first and the last group aim at kGroupRamp times the budget (they run
-// in launches of their own: the column pass alone before the first fused
-// launch, the row pass alone after the last), the others split the rest
-// evenly into the fewest groups of at most about the budget.
-ffst_status plan_regroup(ffst_plan_s* p, double mb) {
+// Plane groups for a budget of `mb` megabytes: runs of consecutive planes
+// cut at targets of the cumulative intermediate size (a plane goes to the
+// group its midpoint falls in).  The first and the last group aim at
+// kGroupRamp times the budget (they run in launches of their own: one pass
+// alone before the first fused launch, the other alone after the last), the
+// others split the rest evenly into the fewest groups of at most about the
+// budget.  Writes each plane's slot offset inside its group to off[] and
+// returns the largest group size (float2 elements).
+static long long build_groups(const ffst_plan_s* p, double mb, std::vector<Group>& groups,
+                              std::vector<long long>& off) {
   const double budget = mb * 1024.0 * 1024.0 / sizeof(float2);
-  const int P = cols_per_cta(p->M);
-  cudaFree(p->d_items);
-  cudaFree(p->d_partials);
-  cudaFree(p->d_H);
-  p->d_items = nullptr;
-  p->d_partials = nullptr;
-  p->d_H = nullptr;
-  p->groups.clear();
+  groups.clear();
+  off.assign(p->eta, 0);
   auto elems_of = [&](int i) { return (long long)p->M * p->planes[i].ldw; };
   double total = 0.0;
   for (int i = 0; i < p->eta; ++i) total += (double)elems_of(i);
@@ -258,7 +264,6 @@ ffst_status plan_regroup(ffst_plan_s* p, double mb) {
     cuts.push_back(e);
     for (int j = 1; j < (ramp ? k + 1 : k); ++j) cuts.push_back(e + rest * j / k);
   }
-  std::vector<ColItem> items;
   Group g{0, 0, 0, 0, 0};
   long long maxg = 0;
   double acc = 0.0;
@@ -270,27 +275,55 @@ ffst_status plan_regroup(ffst_plan_s* p, double mb) {
     size_t k = 0;
     while (k < cuts.size() && cuts[k] <= mid) ++k;
     if (g.p1 > g.p0 && k != gk) {
-      g.nitems = (int)items.size() - g.item0;
-      p->groups.push_back(g);
+      g.nitems = p->planes[i].item0 - g.item0;
+      groups.push_back(g);
       maxg = std::max(maxg, g.elems);
-      g = Group{i, i, 0, (int)items.size(), 0};
+      g = Group{i, i, 0, p->planes[i].item0, 0};
     }
     gk = k;
-    p->planes[i].off = g.elems;
-    p->planes[i].item0 = (int)items.size();
-    for (int c = p->planes[i].c0al; c < p->planes[i].c0 + p->planes[i].W; c += P) items.push_back(ColItem{i, c});
-    p->planes[i].nitems = (int)items.size() - p->planes[i].item0;
+    off[i] = g.elems;
     g.elems += el;
     g.p1 = i + 1;
   }
-  g.nitems = (int)items.size() - g.item0;
-  p->groups.push_back(g);
-  maxg = std::max(maxg, g.elems);
-  p->h_elems = maxg;
-  p->group_mb = mb;
+  g.nitems = p->total_items - g.item0;
+  groups.push_back(g);
+  return std::max(maxg, g.elems);
+}
+
+// (Re)build the forward column work items, the plane groups of both
+// directions and the double-buffered intermediate (sized for the larger
+// group of either direction).
+ffst_status plan_regroup(ffst_plan_s* p, double fwd_mb, double inv_mb) {
+  const int P = cols_per_cta(p->M);
+  cudaFree(p->d_items);
+  cudaFree(p->d_partials);
+  cudaFree(p->d_H);
+  p->d_items = nullptr;
+  p->d_partials = nullptr;
+  p->d_H = nullptr;
+  // forward column items: the 2-column panels of every plane's slot, in plane order
+  std::vector<ColItem> items;
+  for (int i = 0; i < p->eta; ++i) {
+    p->planes[i].item0 = (int)items.size();
+    for (int c = p->planes[i].c0al; c < p->planes[i].c0 + p->planes[i].W; c += P) items.push_back(ColItem{i, c});
+    p->planes[i].nitems = (int)items.size() - p->planes[i].item0;
+  }
   p->total_items = (int)items.size();
+  std::vector<long long> off_f, off_i;
+  const long long hf = build_groups(p, fwd_mb, p->groups, off_f);
+  const long long hi = build_groups(p, inv_mb, p->groups_inv, off_i);
+  p->h_elems = std::max(hf, hi);
+  p->group_mb = fwd_mb;
+  p->group_mb_inv = inv_mb;
+  std::vector<PlaneDesc> pi = p->planes;
+  for (int i = 0; i < p->eta; ++i) {
+    p->planes[i].off = off_f[i];
+    pi[i].off = off_i[i];
+  }
   cudaError_t e = cudaMemcpy(p->d_planes, p->planes.data(), p->planes.size() * sizeof(PlaneDesc),
                              cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !p->d_planes_inv) e = cudaMalloc(&p->d_planes_inv, pi.size() * sizeof(PlaneDesc));
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_planes_inv, pi.data(), pi.size() * sizeof(PlaneDesc), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "plane descriptors");
   if (!items.empty()) {
     if ((e = cudaMalloc(&p->d_items, items.size() * sizeof(ColItem))) != cudaSuccess) return cuda_fail(e, "items");
@@ -301,7 +334,7 @@ ffst_status plan_regroup(ffst_plan_s* p, double mb) {
   }
   if (p->h_elems > 0 && (e = cudaMalloc(&p->d_H, 2 * (size_t)p->h_elems * sizeof(float2))) != cudaSuccess)
     return cuda_fail(e, "workspace H");
-  return tma_build(p);
+  return tma_build(p, off_f, off_i);
 }
 
 // Pass twiddle table of a line (L, E) (layout in ffst_fft.cuh), FP64 -> FP32.
@@ -457,11 +490,11 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
     if (e != cudaSuccess) return cuda_fail(e, "ffst_plan row ranges");
   }
 
-  // groups and forward column work items (budget: autotune cache, FFST_GROUP_MB, default)
+  // groups and forward column work items (budgets: autotune cache, FFST_GROUP_MB*, defaults)
   {
-    double mb = 0.0;
-    if (!autotune_lookup(p.get(), FFST_STORE_F32, &mb)) mb = default_group_mb();
-    const ffst_status st = plan_regroup(p.get(), mb);
+    double fmb = 0.0, imb = 0.0;
+    if (!autotune_lookup(p.get(), FFST_STORE_F32, &fmb, &imb)) default_group_mb(&fmb, &imb);
+    const ffst_status st = plan_regroup(p.get(), fmb, imb);
     if (st != FFST_OK) return st;
   }
 

@@ -84,6 +84,7 @@ def test_batch_and_graph_argument_errors_on_host(lib):
     assert lib.ffst_batch_info(None, 0, None, None, None, None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_forward_batched(None, None, None, 0, None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_graph_launch(None, None) == _lib.FFST_ERR_INVALID_ARG
-    assert lib.ffst_plan_autotune(None, 0, 1, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_plan_autotune(None, 0, 1, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_plan_group_mb(None, None, None) == _lib.FFST_ERR_INVALID_ARG
     lib.ffst_graph_destroy(None)
     lib.ffst_batch_destroy(None)

@@ -96,14 +96,17 @@ def test_autotune_round_trip(ffst, tmp_path):
         x = torch.from_numpy(inputs.scaled_cartoon(512, 512, seed=1)).cuda()
         p = ffst.Plan(512, 512)
         before = p.forward(x).clone()
-        mb = p.autotune(reps=2)
-        assert mb in (32.0, 64.0, 96.0, 128.0, 192.0)
-        assert p.group_mb == mb
+        rec_before = p.inverse(before).clone()
+        fmb, imb = p.autotune(reps=2)
+        cands = (32.0, 64.0, 96.0, 128.0, 192.0)
+        assert fmb in cands and imb in cands
+        assert p.group_mb == (fmb, imb)
         after = p.forward(x)
         assert torch.equal(before, after)  # the grouping does not change results
+        assert torch.equal(rec_before, p.inverse(after))
         text = cache.read_text().strip().splitlines()
-        assert len(text) == 1 and text[0].endswith(" %g" % mb) and " 512 512 4 0 " in text[0]
-        q = ffst.Plan(512, 512)  # picks the cached budget up
-        assert q.group_mb == mb
+        assert len(text) == 1 and text[0].endswith(" %g %g" % (fmb, imb)) and " 512 512 4 0 " in text[0]
+        q = ffst.Plan(512, 512)  # picks the cached budgets up
+        assert q.group_mb == (fmb, imb)
     finally:
         del os.environ["FFST_AUTOTUNE_CACHE"]
