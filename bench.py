@@ -393,10 +393,10 @@ def _time_steps(fn, steps, dev):
 
 
 def run_forms(plan, pool, stack, rec, plain_value, args, dev):
-    """The three forms beside the plain FP32 round trip, each timed like the
-    plain step and with its accuracy measured on the GPU against the plain
-    FP32 path (reconstruction error; coefficient error of low-precision
-    storage against the FP32 stack)."""
+    """The forms beside the plain FP32 round trip, each timed like the plain
+    step and with its accuracy measured on the GPU against the plain FP32
+    path (reconstruction error; coefficient error of low-precision storage
+    against the FP32 stack; d(i) against the stored stack)."""
     import torch
 
     import paper_1202_1773_gb300 as ffst
@@ -436,6 +436,21 @@ def run_forms(plan, pool, stack, rec, plain_value, args, dev):
                      "roofline_step_frac": byts / (ms / 1e3) / 1e9 / _peaks()[0],
                      "accuracy": {"coeff_rel_l2_vs_f32": cerr, "reconstruction_rel_l2": rerr, "tolerance": tol}}
         del lp
+
+    # fused per-plane statistics + soft shrinkage in the forward's row pass,
+    # then the inverse (one denoising round trip), against the plain round trip
+    d0 = plan.forward_stats(x0, out=stack)[1]
+    thr = (1.5 * d0).contiguous()
+    thr[0] = 0.0
+    ms = _time_steps(lambda q: (plan.forward_stats(pool[q % len(pool)], shrink="soft", thresh=thr, out=stack),
+                                plan.inverse(stack, out=rec)), steps, dev)
+    plan.forward_stats(x0, shrink="soft", thresh=thr, out=stack)
+    kept = float(sum(int(torch.count_nonzero(stack[i])) for i in range(eta))) / cps
+    dref = torch.stack([ref[i].double().abs().mean() for i in range(eta)])  # plane by plane
+    dmax = float(((d0.double() - dref).abs() / dref.clamp_min(1e-30)).max())
+    out["stats_soft"] = {"value": cps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                         "vs_plain": cps / (ms / 1e3) / plain_value, "threshold": "1.5 d(i) per plane, low-pass kept",
+                         "kept_fraction": kept, "accuracy": {"mean_abs_rel_vs_stack_max": dmax}}
 
     # batched: 256 images of uneven sizes, forward + inverse replayed from one CUDA graph
     del ref

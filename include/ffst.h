@@ -109,6 +109,24 @@ ffst_status ffst_forward(ffst_plan_t plan, const float* img, void* coeffs, int s
                          float* plane_scale, void* stream);
 
 /*
+ * Forward transform with fused per-plane statistics and shrinkage (the
+ * denoising use named in Sec. 1; the row pass applies them to each
+ * coefficient before it is stored, so the unthresholded stack is never
+ * written).  Arguments as ffst_forward, plus:
+ *   shrink    0: none, 1: soft, c <- sign(c) max(|c| - tau_i, 0),
+ *             2: hard, c <- c if |c| > tau_i else 0;
+ *   thresh    device [eta] float, tau_i per plane (required when shrink != 0;
+ *             in units of the coefficients c, independent of the storage
+ *             scale s_i);
+ *   mean_abs  device [eta] float or NULL: receives d(i) = 1/(MN) sum |c_i|
+ *             (Sec. 3.5.2 eq. shearlet_meanvalue) of the coefficients before
+ *             shrinkage, summed in a fixed order (deterministic).
+ * Returns FFST_ERR_INVALID_ARG for another shrink code or a missing thresh.
+ */
+ffst_status ffst_forward_stats(ffst_plan_t plan, const float* img, void* coeffs, int storage, float* plane_scale,
+                               int shrink, const float* thresh, float* mean_abs, void* stream);
+
+/*
  * Inverse transform, Sec. 3.3 eq. (inverseShearletTransform), normalised by
  * sum_i psi_hat_i^2 (which the Parseval frame of Sec. 3.2 makes 1).
  *   coeffs:      device [eta][rows][cols] of the storage type, read only.

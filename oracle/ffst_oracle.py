@@ -17,7 +17,10 @@ Shearlet Transform: a tutorial", arXiv:1202.1773):
 * plane index i <-> (kappa, j, k), eta = 2^{j0+2} - 3: Sec. 3.5.2;
 * forward transform: Sec. 3.1 eq. (shearletTransform);
 * inverse transform: Sec. 3.3 eq. (inverseShearletTransform);
-* real-coefficient mirroring of the Nyquist row/column: Sec. 3.8.1.
+* real-coefficient mirroring of the Nyquist row/column: Sec. 3.8.1;
+* per-plane mean |c| d(i): Sec. 3.5.2 eq. (shearlet_meanvalue); soft and
+  hard shrinkage of the coefficients (denoising, named in Sec. 1; textbook
+  definitions, the paper gives none).
 
 Readings of passages where the paper is silent or ambiguous (each is listed
 in the project's design notes):
@@ -361,3 +364,21 @@ def mean_abs(c: np.ndarray) -> np.ndarray:
     """d(i) = 1/(MN) sum |c(., ., i)|, Sec. 3.5.2 eq. (shearlet_meanvalue)."""
     c = np.asarray(c)
     return np.abs(c).reshape(c.shape[0], -1).mean(axis=1)
+
+
+def shrink(c: np.ndarray, tau, mode: str) -> np.ndarray:
+    """Per-plane coefficient shrinkage for denoising (an application the
+    paper names in Sec. 1; it defines no operator).  The textbook forms, with
+    tau[i] the threshold of plane i (a scalar applies to every plane):
+
+    * soft: sign(c) * max(|c| - tau, 0)
+    * hard: c where |c| > tau, else 0
+    """
+    c = np.asarray(c, dtype=np.float64)
+    t = np.broadcast_to(np.asarray(tau, dtype=np.float64).reshape(-1, *([1] * (c.ndim - 1))), c.shape) \
+        if np.ndim(tau) else np.full(c.shape, float(tau))
+    if mode == "soft":
+        return np.sign(c) * np.maximum(np.abs(c) - t, 0.0)
+    if mode == "hard":
+        return np.where(np.abs(c) > t, c, 0.0)
+    raise ValueError(f"unknown shrinkage mode {mode!r}")

@@ -46,6 +46,7 @@ from ._lib import (  # noqa: F401
     ffst_plan_set_schedule,
     ffst_forward,
     ffst_forward_noalloc,
+    ffst_forward_stats,
     ffst_inverse,
     ffst_plan,
     ffst_plan_info,
@@ -150,6 +151,36 @@ class Plan:
         ffst_forward(self.handle, img, out, storage, plane_scale if storage != FFST_STORE_F32 else None,
                      self._stream())
         return (out, plane_scale) if storage != FFST_STORE_F32 else out
+
+    def forward_stats(self, img, shrink=None, thresh=None, dtype=None, out=None, plane_scale=None):
+        """Forward with fused per-plane statistics and optional shrinkage.
+
+        shrink: None, "soft" or "hard"; thresh: per-plane thresholds (tensor
+        [eta] on the device, or a float for every plane).  Returns
+        (coeffs, mean_abs) with mean_abs[i] = d(i) of the unthresholded
+        coefficients, plus the plane scales for float16/bfloat16 storage.
+        """
+        torch = _torch()
+        self._check_img(img)
+        if out is None:
+            out = torch.empty(self.shape, dtype=dtype or torch.float32, device=self.device)
+        self._check_coeffs(out)
+        storage = _storage_of(out.dtype)
+        if storage != FFST_STORE_F32 and plane_scale is None:
+            plane_scale = torch.empty(self.num_planes, dtype=torch.float32, device=self.device)
+        code = {None: 0, "soft": 1, "hard": 2}.get(shrink)
+        if code is None:
+            raise ValueError(f"shrink must be None, 'soft' or 'hard', not {shrink!r}")
+        if code and thresh is None:
+            raise ValueError("thresh is required for shrinkage")
+        if code and not torch.is_tensor(thresh):
+            thresh = torch.full((self.num_planes,), float(thresh), dtype=torch.float32, device=self.device)
+        mean_abs = torch.empty(self.num_planes, dtype=torch.float32, device=self.device)
+        ffst_forward_stats(self.handle, img, out, storage, plane_scale if storage != FFST_STORE_F32 else None, code,
+                           thresh if code else None, mean_abs, self._stream())
+        if storage != FFST_STORE_F32:
+            return out, mean_abs, plane_scale
+        return out, mean_abs
 
     def _synth(self, fn, coeffs, plane_scale, out):
         torch = _torch()

@@ -38,6 +38,7 @@ SIGNATURES = [
     ("ffst_inverse", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
     ("ffst_adjoint", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
     ("ffst_forward_noalloc", _I, [_I, _I, _I, _VP, _VP, _VP]),
+    ("ffst_forward_stats", _I, [_VP, _VP, _VP, _I, _VP, _I, _VP, _VP, _VP]),
     ("ffst_plan_autotune", _I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("ffst_plan_group_mb", _I, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("ffst_plan_set_schedule", _I, [_VP, _I]),
@@ -149,6 +150,11 @@ def ffst_spectra(plan: int, psi, stream=None):
 
 def ffst_forward(plan: int, img, coeffs, storage: int = FFST_STORE_F32, plane_scale=None, stream=None):
     _check("ffst_forward", lib().ffst_forward(plan, _ptr(img), _ptr(coeffs), int(storage), _ptr(plane_scale), stream))
+
+
+def ffst_forward_stats(plan: int, img, coeffs, storage: int, plane_scale, shrink: int, thresh, mean_abs, stream: int):
+    _check("ffst_forward_stats", lib().ffst_forward_stats(plan, _ptr(img), _ptr(coeffs), int(storage), _ptr(plane_scale),
+                                                          int(shrink), _ptr(thresh), _ptr(mean_abs), stream))
 
 
 def ffst_inverse(plan: int, coeffs, storage: int, plane_scale, img, stream=None):

@@ -84,8 +84,15 @@ static FwdColsArgs fwd_cols_args(const ffst_plan_s* p, const Group& g, float2* H
   return a;
 }
 
+// Fused per-plane statistics and shrinkage of a forward (ffst_forward_stats).
+struct StatsOpts {
+  int shrink = 0;               // 0 none, 1 soft, 2 hard
+  const float* thresh = nullptr;
+  bool stats = false;           // accumulate sum |c| per (plane, row block)
+};
+
 static C2RArgs plane_c2r_args(const ffst_plan_s* p, const Group& g, const float2* H, void* coeffs, int storage,
-                              const float* plane_scale) {
+                              const float* plane_scale, const StatsOpts* so = nullptr) {
   const long long plane = (long long)p->M * p->N;
   C2RArgs a;
   a.src = H;
@@ -102,6 +109,10 @@ static C2RArgs plane_c2r_args(const ffst_plan_s* p, const Group& g, const float2
   a.scale = 1.0f;  // fwd_cols already applied 1/(M N) (and the R2C gain)
   a.tw = p->d_tw_rows;
   a.rtw = p->d_rtw;
+  a.shrink = so ? so->shrink : 0;
+  a.thresh = so ? so->thresh : nullptr;
+  a.abs_partials = (so && so->stats) ? p->d_abs_partials : nullptr;
+  a.rbx = p->row_blocks;
   return a;
 }
 
@@ -142,7 +153,7 @@ static InvColsArgs inv_cols_args(const ffst_plan_s* p, const Group& g, const flo
 }
 
 static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int storage, float* plane_scale,
-                            cudaStream_t s) {
+                            cudaStream_t s, const StatsOpts* so = nullptr) {
   const long long plane = (long long)p->M * p->N;
   const int esz = storage == FFST_STORE_F32 ? 4 : 2;
   const int Lr = p->N / 2;
@@ -178,7 +189,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
     const Group all = all_planes(p);
     e = timed(p, kTimeFwdSched, (double)p->eta * plane * esz, s, [&] {
       return launch_fwd_sched(p, fwd_cols_args(p, all, nullptr, partials),
-                              plane_c2r_args(p, all, nullptr, coeffs, storage, nullptr), target,
+                              plane_c2r_args(p, all, nullptr, coeffs, storage, nullptr, so), target,
                               partials ? plane_scale : nullptr, s);
     });
   } else if (use_fused(p)) {
@@ -192,7 +203,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
       const double by = (double)(rg.p1 - rg.p0) * plane * esz;
       e = timed(p, kTimeFwdFused, by, s, [&] {
         return launch_fwd_fused(p->M, fwd_cols_args(p, cg, hbuf(p, g), partials), cg.nitems,
-                                plane_c2r_args(p, rg, hbuf(p, g - 1), coeffs, storage, plane_scale), rg.p1 - rg.p0,
+                                plane_c2r_args(p, rg, hbuf(p, g - 1), coeffs, storage, plane_scale, so), rg.p1 - rg.p0,
                                 s);
       });
       if (e == cudaSuccess) e = scales(g);
@@ -200,7 +211,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
     if (e == cudaSuccess) {
       const Group& rg = p->groups[G - 1];
       e = timed(p, kTimeFwdRows, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
-        return launch_rows_c2r(Lr, plane_c2r_args(p, rg, hbuf(p, G - 1), coeffs, storage, plane_scale),
+        return launch_rows_c2r(Lr, plane_c2r_args(p, rg, hbuf(p, G - 1), coeffs, storage, plane_scale, so),
                                rg.p1 - rg.p0, s);
       });
     }
@@ -214,7 +225,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
       if (e == cudaSuccess) e = scales(g);
       if (e == cudaSuccess)
         e = timed(p, kTimeFwdRows, (double)(gr.p1 - gr.p0) * plane * esz, s, [&] {
-          return launch_rows_c2r(Lr, plane_c2r_args(p, gr, hbuf(p, g), coeffs, storage, plane_scale), gr.p1 - gr.p0,
+          return launch_rows_c2r(Lr, plane_c2r_args(p, gr, hbuf(p, g), coeffs, storage, plane_scale, so), gr.p1 - gr.p0,
                                  s);
         });
     }
@@ -310,6 +321,26 @@ extern "C" ffst_status ffst_forward(ffst_plan_t plan, const float* img, void* co
   ffst_status st = check_storage(storage, plane_scale, "ffst_forward");
   if (st != FFST_OK) return st;
   return analysis(plan, img, coeffs, storage, plane_scale, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" ffst_status ffst_forward_stats(ffst_plan_t plan, const float* img, void* coeffs, int storage,
+                                          float* plane_scale, int shrink, const float* thresh, float* mean_abs,
+                                          void* stream) {
+  if (!plan || !img || !coeffs) return fail(FFST_ERR_INVALID_ARG, "ffst_forward_stats: NULL argument");
+  ffst_status st = check_storage(storage, plane_scale, "ffst_forward_stats");
+  if (st != FFST_OK) return st;
+  if (shrink < 0 || shrink > 2) return fail(FFST_ERR_INVALID_ARG, "ffst_forward_stats: shrink must be 0, 1 or 2");
+  if (shrink && !thresh) return fail(FFST_ERR_INVALID_ARG, "ffst_forward_stats: thresh is required for shrinkage");
+  StatsOpts so;
+  so.shrink = shrink;
+  so.thresh = thresh;
+  so.stats = mean_abs != nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = analysis(plan, img, coeffs, storage, plane_scale, s, &so);
+  if (st != FFST_OK || !mean_abs) return st;
+  const cudaError_t e = timed(plan, kTimeOther, 0.0, s, [&] { return launch_mean_abs(plan, mean_abs, s); });
+  if (e != cudaSuccess) return cuda_fail(e, "ffst_forward_stats mean |c|");
+  return FFST_OK;
 }
 
 extern "C" ffst_status ffst_inverse(ffst_plan_t plan, const void* coeffs, int storage, const float* plane_scale,

@@ -128,6 +128,22 @@ __global__ void k_plane_scales(const PlaneDesc* __restrict__ planes, int p0, int
   plane_scale[p] = plane_scale_of(partials, planes[p].item0, planes[p].nitems, target);
 }
 
+// d(i) = 1/(MN) sum |c_i| from the row pass's per-block partial sums
+// (Sec. 3.5.2 eq. shearlet_meanvalue), summed in block order.
+__global__ void k_mean_abs(const float* __restrict__ partials, int rbx, int eta, float inv_mn, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= eta) return;
+  float sum = 0.0f;
+  for (int b = 0; b < rbx; ++b) sum += partials[(long long)i * rbx + b];
+  out[i] = sum * inv_mn;
+}
+
+cudaError_t launch_mean_abs(const ffst_plan_s* p, float* mean_abs, cudaStream_t s) {
+  k_mean_abs<<<(p->eta + 127) / 128, 128, 0, s>>>(p->d_abs_partials, p->row_blocks, p->eta,
+                                                 1.0f / ((float)p->M * (float)p->N), mean_abs);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_plane_scales(const ffst_plan_s* p, const Group& g, const float* partials, float target,
                                 float* plane_scale, cudaStream_t s) {
   const int n = g.p1 - g.p0;

@@ -274,6 +274,8 @@ struct ffst_plan_s {
   CUtensorMap* d_tmaps = nullptr;       // per plane: TMA map of its forward slot (or null)
   CUtensorMap* d_tmaps_inv = nullptr;   // per plane: TMA map of its inverse slot (or null)
   int* d_err = nullptr;                 // sticky device error word (bounded waits), read by ffst_plan_check
+  float* d_abs_partials = nullptr;      // [eta][row_blocks] sum |c| per row block (ffst_forward_stats)
+  int row_blocks = 0;                   // row-pass blocks per plane
   ffst::Sched sched;
   int sched_mode = 0;                   // 0: grouped launches, 1: persistent, 2: persistent with a stuck wait (test)
   ffst::Timer timer;
@@ -302,11 +304,14 @@ cudaError_t launch_ranges(const ffst_plan_s* p, cudaStream_t s);
 cudaError_t launch_inv_norm(const ffst_plan_s* p, cudaStream_t s);
 cudaError_t launch_plane_scales(const ffst_plan_s* p, const Group& g, const float* partials, float target,
                                 float* plane_scale, cudaStream_t s);
+cudaError_t launch_mean_abs(const ffst_plan_s* p, float* mean_abs, cudaStream_t s);
 
-// Opt a kernel into more than 48 KB of dynamic shared memory (once per kernel).
+// Opt a kernel into more than 48 KB of shared memory.  The kernels also
+// hold up to 1 KB of static shared memory (reductions, barriers), which
+// counts against the default 48 KB.
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes + 1024 <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 

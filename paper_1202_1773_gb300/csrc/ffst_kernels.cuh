@@ -172,6 +172,11 @@ struct C2RArgs {
   float scale;               // output factor (1 when the producer already normalised)
   const float2* tw;
   const float2* rtw;
+  // fused per-plane statistics and shrinkage of the coefficients c (plane rows only)
+  int shrink;                // 0 none, 1 soft, 2 hard
+  const float* thresh;       // per-plane threshold on |c| (shrink != 0)
+  float* abs_partials;       // per (plane, row block): sum |c| before shrinkage, or null
+  int rbx;                   // row blocks per plane (stride of abs_partials)
 };
 
 // Factor s_i of plane a.plane0 + by for low-precision storage (1 otherwise),
@@ -242,6 +247,38 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
     for (int m = 0; m < E; ++m) v[m] = make_float2(v[m].x * s, v[m].y * s);
   }
   line_fft<L, E, true, RowCfg<L>::SYNC>(v, buf, t, a.tw, 1 + team);
+  if (a.shrink || a.abs_partials) {  // uniform over the launch
+    // v holds c * ps: threshold and statistics act on c (ps is a power of two)
+    __shared__ float red[kThreads / 32];
+    const float tau = a.shrink ? __ldg(&a.thresh[plane]) * ps : 0.0f;
+    float acc = 0.0f;
+    if (act) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        float x = v[m].x, y = v[m].y;
+        acc += fabsf(x) + fabsf(y);
+        if (a.shrink == 1) {
+          x = copysignf(fmaxf(fabsf(x) - tau, 0.0f), x);
+          y = copysignf(fmaxf(fabsf(y) - tau, 0.0f), y);
+        } else if (a.shrink == 2) {
+          x = fabsf(x) > tau ? x : 0.0f;
+          y = fabsf(y) > tau ? y : 0.0f;
+        }
+        v[m] = make_float2(x, y);
+      }
+    }
+    if (a.abs_partials) {  // fixed reduction order: deterministic
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float sum = 0.0f;
+        for (int q = 0; q < kThreads / 32; ++q) sum += red[q];
+        a.abs_partials[(long long)plane * a.rbx + bx] = sum / ps;
+      }
+    }
+  }
   if (!act) return;
   void* dst = static_cast<char*>(a.dst) + (long long)by * a.dst_plane_stride * stor_bytes(a.st);
   const long long rbase = (long long)row * N + 2 * t;

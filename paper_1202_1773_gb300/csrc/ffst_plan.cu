@@ -199,6 +199,7 @@ static void free_plan(ffst_plan_s* p) {
   cudaFree(p->d_partials);
   cudaFree(p->d_items);
   cudaFree(p->d_err);
+  cudaFree(p->d_abs_partials);
   tma_free(p);
   sched_free(p);
   for (auto& r : p->timer.pending) {
@@ -503,6 +504,12 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
   if ((e = cudaMalloc(&p->d_F, spec * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "workspace F");
   if ((e = cudaMalloc(&p->d_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(p->d_err, 0, sizeof(int))) != cudaSuccess)
     return cuda_fail(e, "error word");
+  {
+    const int L = cols / 2, teams = kThreads / (L / row_E(L));
+    p->row_blocks = (rows + teams - 1) / teams;
+    if ((e = cudaMalloc(&p->d_abs_partials, sizeof(float) * (size_t)p->eta * p->row_blocks)) != cudaSuccess)
+      return cuda_fail(e, "statistics partials");
+  }
   if ((e = cudaMalloc(&p->d_S, spec * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "workspace S");
   if ((e = cudaMalloc(&p->d_invD, spec * sizeof(float))) != cudaSuccess) return cuda_fail(e, "normalisation");
   if ((e = launch_inv_norm(p.get(), 0)) != cudaSuccess) return cuda_fail(e, "ffst_plan normalisation");

@@ -146,3 +146,31 @@ def test_mean_abs_vector():
     d = o.mean_abs(o.forward(f))
     assert d[0] == pytest.approx(0.75, abs=1e-14)
     assert np.all(d[1:] <= 1e-14)
+
+
+def test_shrink_closed_forms():
+    # textbook soft / hard thresholding, per plane thresholds broadcast over the plane
+    c = np.array([[[3.0, -0.5], [1.0, -2.5]], [[0.2, -0.2], [4.0, 0.0]]])
+    tau = np.array([1.0, 0.5])
+    np.testing.assert_array_equal(o.shrink(c, tau, "soft"), [[[2.0, 0.0], [0.0, -1.5]], [[0.0, 0.0], [3.5, 0.0]]])
+    np.testing.assert_array_equal(o.shrink(c, tau, "hard"), [[[3.0, 0.0], [0.0, -2.5]], [[0.0, 0.0], [4.0, 0.0]]])
+    np.testing.assert_array_equal(o.shrink(c, 0.0, "soft"), c)  # zero threshold: identity
+    np.testing.assert_array_equal(o.shrink(c, 0.0, "hard"), np.where(c != 0, c, 0.0))
+    with pytest.raises(ValueError):
+        o.shrink(c, 1.0, "median")
+
+
+def test_shrink_invariants():
+    rng = np.random.default_rng(4)
+    c = rng.normal(size=(3, 16, 16))
+    a, b = 0.3, 0.45
+    s = o.shrink(c, a, "soft")
+    assert np.all(np.abs(s) <= np.abs(c)) and np.all(s * c >= 0)  # shrinks toward 0, keeps signs
+    np.testing.assert_allclose(o.shrink(s, b, "soft"), o.shrink(c, a + b, "soft"), atol=1e-15)  # semigroup
+    h = o.shrink(c, a, "hard")
+    np.testing.assert_array_equal(o.shrink(h, a, "hard"), h)  # idempotent
+    # soft = hard minus tau*sign on the kept entries
+    np.testing.assert_allclose(s, np.where(h != 0, h - a * np.sign(h), 0.0), atol=1e-15)
+    # the low-pass plane of a constant image is the value itself: shrinking it is a scalar map
+    d = o.forward(np.full((32, 32), 0.75))
+    np.testing.assert_allclose(o.shrink(d, 0.25, "soft")[0], 0.5, atol=1e-13)
