@@ -11,6 +11,8 @@ Shearlet Transform: a tutorial", arXiv:1202.1773):
 
 * windows ``v``, ``b``, ``psi1_hat``, ``psi2_hat``, ``varphi``, ``phi_hat``:
   Sec. 2.1 eqs. (v), (b), (Psi1), (Psi2) and Sec. 2.4 eq. (phi);
+* smooth shearlets (``smooth=True``): ``Phi_hat`` Sec. 2.4 eq. (Phi) and
+  ``Psi1_hat`` Sec. 3.4 eqs. (newPsi1), (smoothPsi);
 * cones C^h, C^v, C^x: Sec. 2.3;
 * discretisation j0, a_j, s_{j,k}, the index set Omega: Sec. 3.1;
 * frequency grid Xi (X = 2^{2 j0 - 1}): Sec. 3.5.1;
@@ -90,6 +92,21 @@ def varphi(omega):
     w = np.abs(np.asarray(omega, dtype=np.float64))
     mid = np.cos(0.5 * np.pi * v(2.0 * w - 1.0))
     return np.where(w <= 0.5, 1.0, np.where(w < 1.0, mid, 0.0))
+
+
+def Phi_hat(w1, w2):
+    """Tensor-product scaling function varphi(w1) varphi(w2), Sec. 2.4 eq. (Phi)."""
+    return varphi(w1) * varphi(w2)
+
+
+def Psi1_hat(w1, w2):
+    """2-D radial window of the smooth shearlets, Sec. 3.4 eq. (newPsi1):
+    sqrt(Phi_hat(w/4)^2 - Phi_hat(w)^2); supported in [-4, 4]^2 minus
+    [-1/2, 1/2]^2."""
+    w1 = np.asarray(w1, dtype=np.float64)
+    w2 = np.asarray(w2, dtype=np.float64)
+    d = Phi_hat(0.25 * w1, 0.25 * w2) ** 2 - Phi_hat(w1, w2) ** 2
+    return np.sqrt(np.maximum(d, 0.0))
 
 
 def phi_hat(xi1, xi2):
@@ -212,7 +229,7 @@ def _ratio(num, den, mask):
     return out
 
 
-def spectrum_raw(rows: int, cols: int, scales: int, i: int) -> np.ndarray:
+def spectrum_raw(rows: int, cols: int, scales: int, i: int, smooth: bool = False) -> np.ndarray:
     """Spectrum of plane i on Xi without the Nyquist fix, FFT storage order.
 
     Sec. 3.1 eq. (shearletTransform):
@@ -221,16 +238,24 @@ def spectrum_raw(rows: int, cols: int, scales: int, i: int) -> np.ndarray:
       v, |k|<J:  psi1(4^-j xi2) psi2(2^j xi1/xi2 + k) on C^v      (eq. verticalShearlet)
       seam |k|=J: the glued sum psi^h + psi^v + psi^x: the h formula on
                   C^h and on the seam lines, the v formula on C^v.
+    smooth=True gives the smooth shearlets of Sec. 3.4 eq. (smoothPsi): the
+    radial factor of both cones is Psi1_hat(4^-j xi) (eq. newPsi1) and the
+    low-pass is the tensor product Phi_hat(xi) (Sec. 2.4 eq. Phi).
     """
     kappa, j, k = plane_table(scales)[i]
     o1, o2, xi1, xi2 = grid(rows, cols, scales)
     if kappa == "lowpass":
-        return phi_hat(xi1, xi2)
+        return Phi_hat(xi1, xi2) if smooth else phi_hat(xi1, xi2)
     ch, cv, cx = cones(rows, cols, o1, o2)
     a = 4.0 ** (-j)
     J = 2.0**j
-    h_part = psi1_hat(a * xi1) * psi2_hat(J * _ratio(xi2, xi1, xi1 != 0) + k)
-    v_part = psi1_hat(a * xi2) * psi2_hat(J * _ratio(xi1, xi2, xi2 != 0) + k)
+    if smooth:
+        r = Psi1_hat(a * xi1, a * xi2)
+        h_part = r * psi2_hat(J * _ratio(xi2, xi1, xi1 != 0) + k)
+        v_part = r * psi2_hat(J * _ratio(xi1, xi2, xi2 != 0) + k)
+    else:
+        h_part = psi1_hat(a * xi1) * psi2_hat(J * _ratio(xi2, xi1, xi1 != 0) + k)
+        v_part = psi1_hat(a * xi2) * psi2_hat(J * _ratio(xi1, xi2, xi2 != 0) + k)
     if kappa == "h":
         return np.where(ch, h_part, 0.0)
     if kappa == "v":
@@ -263,30 +288,32 @@ def nyquist_mirror(psi: np.ndarray) -> np.ndarray:
     return out
 
 
-def spectrum(rows: int, cols: int, scales: int, i: int, real_fix: bool = True) -> np.ndarray:
+def spectrum(rows: int, cols: int, scales: int, i: int, real_fix: bool = True, smooth: bool = False) -> np.ndarray:
     """Spectrum psi_hat_i of plane i (FFT storage order), fix applied by default.
 
     The fix is on by default, as the paper's ``realReal`` option (Sec. 3.5.3).
     """
-    raw = spectrum_raw(rows, cols, scales, i)
+    raw = spectrum_raw(rows, cols, scales, i, smooth)
     return nyquist_mirror(raw) if real_fix else raw
 
 
-def spectra(rows: int, cols: int, scales: int | None = None, real_fix: bool = True) -> np.ndarray:
+def spectra(rows: int, cols: int, scales: int | None = None, real_fix: bool = True,
+            smooth: bool = False) -> np.ndarray:
     """Stack of all eta spectra, shape (eta, M, N), Sec. 3.5.2."""
     if scales is None:
         scales = default_scales(rows, cols)
-    return np.stack([spectrum(rows, cols, scales, i, real_fix)
+    return np.stack([spectrum(rows, cols, scales, i, real_fix, smooth)
                      for i in range(num_planes(scales))])
 
 
-def frame_sum(rows: int, cols: int, scales: int | None = None, real_fix: bool = True) -> np.ndarray:
+def frame_sum(rows: int, cols: int, scales: int | None = None, real_fix: bool = True,
+              smooth: bool = False) -> np.ndarray:
     """sum_i psi_hat_i^2 on the grid (Sec. 3.6, frame tightness)."""
     if scales is None:
         scales = default_scales(rows, cols)
     acc = np.zeros((rows, cols))
     for i in range(num_planes(scales)):
-        acc += spectrum(rows, cols, scales, i, real_fix) ** 2
+        acc += spectrum(rows, cols, scales, i, real_fix, smooth) ** 2
     return acc
 
 
@@ -306,13 +333,13 @@ def forward_complex(f: np.ndarray, scales: int | None = None, real_fix: bool = T
                      for i in range(num_planes(scales))])
 
 
-def forward_plane(F: np.ndarray, scales: int, i: int) -> np.ndarray:
+def forward_plane(F: np.ndarray, scales: int, i: int, smooth: bool = False) -> np.ndarray:
     """One real coefficient plane from a precomputed F = fft2(f)."""
     M, N = F.shape
-    return np.real(np.fft.ifft2(spectrum(M, N, scales, i) * F))
+    return np.real(np.fft.ifft2(spectrum(M, N, scales, i, smooth=smooth) * F))
 
 
-def forward(f: np.ndarray, scales: int | None = None) -> np.ndarray:
+def forward(f: np.ndarray, scales: int | None = None, smooth: bool = False) -> np.ndarray:
     """Real coefficient stack (eta, M, N): the real part of ``forward_complex``.
 
     With the Nyquist fix the imaginary part is rounding noise (Sec. 3.8.1).
@@ -322,10 +349,10 @@ def forward(f: np.ndarray, scales: int | None = None) -> np.ndarray:
     if scales is None:
         scales = default_scales(M, N)
     F = np.fft.fft2(f)
-    return np.stack([forward_plane(F, scales, i) for i in range(num_planes(scales))])
+    return np.stack([forward_plane(F, scales, i, smooth) for i in range(num_planes(scales))])
 
 
-def adjoint(c: np.ndarray, scales: int | None = None) -> np.ndarray:
+def adjoint(c: np.ndarray, scales: int | None = None, smooth: bool = False) -> np.ndarray:
     """T* c = Re ifft2( sum_i psi_hat_i * fft2(c_i) ), Sec. 3.3.
 
     For a Parseval frame T* = T^-1 (Sec. 3.2, eq. shearlet_transform_as_matrix).
@@ -336,11 +363,11 @@ def adjoint(c: np.ndarray, scales: int | None = None) -> np.ndarray:
         scales = default_scales(M, N)
     acc = np.zeros((M, N), dtype=np.complex128)
     for i in range(num_planes(scales)):
-        acc += spectrum(M, N, scales, i) * np.fft.fft2(c[i])
+        acc += spectrum(M, N, scales, i, smooth=smooth) * np.fft.fft2(c[i])
     return np.real(np.fft.ifft2(acc))
 
 
-def inverse(c: np.ndarray, scales: int | None = None) -> np.ndarray:
+def inverse(c: np.ndarray, scales: int | None = None, smooth: bool = False) -> np.ndarray:
     """Re ifft2( sum_i psi_hat_i * fft2(c_i) / sum_i psi_hat_i^2 ), Sec. 3.3.
 
     Sec. 3.3 eq. (inverseShearletTransform) sums the products; the division
@@ -354,7 +381,7 @@ def inverse(c: np.ndarray, scales: int | None = None) -> np.ndarray:
     acc = np.zeros((M, N), dtype=np.complex128)
     den = np.zeros((M, N))
     for i in range(num_planes(scales)):
-        s = spectrum(M, N, scales, i)
+        s = spectrum(M, N, scales, i, smooth=smooth)
         acc += s * np.fft.fft2(c[i])
         den += s * s
     return np.real(np.fft.ifft2(acc / den))
