@@ -452,6 +452,15 @@ def run_forms(plan, pool, stack, rec, plain_value, args, dev):
                          "vs_plain": cps / (ms / 1e3) / plain_value, "threshold": "1.5 d(i) per plane, low-pass kept",
                          "kept_fraction": kept, "accuracy": {"mean_abs_rel_vs_stack_max": dmax}}
 
+    # smooth shearlets (Sec. 3.4): a plan of the same size, same round trip
+    sp = ffst.Plan(ROWS, COLS, SCALES, device=dev, smooth=True)
+    ms = _time_steps(lambda q: (sp.forward(pool[q % len(pool)], out=stack), sp.inverse(stack, out=rec)), steps, dev)
+    sp.forward(x0, out=stack)
+    err = float(torch.linalg.norm(sp.inverse(stack) - x0)) / xnorm
+    out["smooth"] = {"value": cps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "vs_plain": cps / (ms / 1e3) / plain_value,
+                     "accuracy": {"reconstruction_rel_l2": err}}
+    sp.close()
+
     # batched: 256 images of uneven sizes, forward + inverse replayed from one CUDA graph
     del ref
     n = 256

@@ -66,6 +66,12 @@ typedef enum {
 /* Plane kinds returned by ffst_plane_index (kappa of Sec. 3.1). */
 enum { FFST_CONE_LOWPASS = 0, FFST_CONE_H = 1, FFST_CONE_V = 2, FFST_CONE_SEAM = 3 };
 
+/* Shearlet constructions (ffst_plan_variant). */
+enum {
+  FFST_VARIANT_CLASSIC = 0, /* Sec. 3.1: radial factor psi1 of one axis per cone, cone low-pass  */
+  FFST_VARIANT_SMOOTH = 1   /* Sec. 3.4: 2-D radial factor Psi1 (eq. newPsi1), tensor low-pass */
+};
+
 /*
  * Build a plan for rows x cols images with `scales` scales (j0 of Sec. 3.1;
  * <= 0 selects j0 = floor(1/2 log2 max(rows, cols))).  The number of planes
@@ -75,6 +81,18 @@ enum { FFST_CONE_LOWPASS = 0, FFST_CONE_H = 1, FFST_CONE_V = 2, FFST_CONE_SEAM =
  * workspace.  Uses the current CUDA device.  On success *out owns all of it.
  */
 ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* out);
+
+/*
+ * As ffst_plan, for the shearlet construction `variant`: FFST_VARIANT_CLASSIC
+ * (what ffst_plan builds) or FFST_VARIANT_SMOOTH, the smooth shearlets of
+ * Sec. 3.4 eqs. (newPsi1), (smoothPsi): every plane's radial factor is
+ * Psi1(4^-j xi) = sqrt(Phi(4^-j xi / 4)^2 - Phi(4^-j xi)^2) with the tensor
+ * scaling function Phi = varphi x varphi of Sec. 2.4 eq. (Phi), which is
+ * also the low-pass.  Same planes, order and Parseval property; every
+ * transform entry point works on either.  FFST_ERR_INVALID_ARG for another
+ * variant code.
+ */
+ffst_status ffst_plan_variant(int rows, int cols, int scales, int variant, ffst_plan_t* out);
 
 /* Query a plan.  Any output pointer may be NULL. */
 ffst_status ffst_plan_info(ffst_plan_t plan, int* rows, int* cols, int* scales, int* num_planes);

@@ -79,13 +79,17 @@ def _storage_of(dtype) -> int:
 
 
 class Plan:
-    """A libffst plan for rows x cols float32 images on one CUDA device."""
+    """A libffst plan for rows x cols float32 images on one CUDA device.
 
-    def __init__(self, rows: int, cols: int, scales: int = 0, device=None):
+    smooth=True builds the smooth shearlets of Sec. 3.4 (ffst_plan_variant).
+    """
+
+    def __init__(self, rows: int, cols: int, scales: int = 0, device=None, smooth: bool = False):
         torch = _torch()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.smooth = bool(smooth)
         with torch.cuda.device(self.device):
-            self.handle = ffst_plan(rows, cols, scales)
+            self.handle = ffst_plan(rows, cols, scales, _lib.FFST_VARIANT_SMOOTH if smooth else _lib.FFST_VARIANT_CLASSIC)
         self.rows, self.cols, self.scales, self.num_planes = ffst_plan_info(self.handle)
 
     # -- bookkeeping ----------------------------------------------------------

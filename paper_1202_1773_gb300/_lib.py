@@ -31,6 +31,7 @@ _VP = ctypes.c_void_p
 _I = ctypes.c_int
 SIGNATURES = [
     ("ffst_plan", _I, [_I, _I, _I, ctypes.POINTER(_VP)]),
+    ("ffst_plan_variant", _I, [_I, _I, _I, _I, ctypes.POINTER(_VP)]),
     ("ffst_plan_info", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("ffst_plane_index", _I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("ffst_spectra", _I, [_VP, _VP, _VP]),
@@ -124,9 +125,17 @@ def _ptr(x) -> int | None:
 
 # --- C-ABI wrappers (same names as the C entry points) -----------------------
 
-def ffst_plan(rows: int, cols: int, scales: int = 0) -> int:
+FFST_VARIANT_CLASSIC = 0
+FFST_VARIANT_SMOOTH = 1
+
+
+def ffst_plan(rows: int, cols: int, scales: int = 0, variant: int = FFST_VARIANT_CLASSIC) -> int:
     out = _VP()
-    _check("ffst_plan", lib().ffst_plan(int(rows), int(cols), int(scales), ctypes.byref(out)))
+    if variant == FFST_VARIANT_CLASSIC:
+        _check("ffst_plan", lib().ffst_plan(int(rows), int(cols), int(scales), ctypes.byref(out)))
+    else:
+        _check("ffst_plan_variant",
+               lib().ffst_plan_variant(int(rows), int(cols), int(scales), int(variant), ctypes.byref(out)))
     return out.value
 
 

@@ -175,6 +175,12 @@ struct WinParams {
   const float* psi1_row;  // [j0][hm+1]: psi1(4^-j * a * dr), a = |omega_2|
   const float* phi_col;   // [hn+1]:     varphi(a * dc)
   const float* phi_row;   // [hm+1]:     varphi(a * dr)
+  // smooth shearlets (Sec. 3.4): per scale j, with w = 4^-j a d (d = dc or dr)
+  int smooth;
+  const float* sig_col;   // [j0][hn+1]: 1 - varphi(w)^2
+  const float* sig_row;   // [j0][hm+1]
+  const float* alp_col;   // [j0][hn+1]: varphi(w / 4)^2
+  const float* alp_row;   // [j0][hm+1]
 };
 
 // One column-panel work item of the forward column pass.
@@ -248,6 +254,7 @@ struct Sched {
 
 struct ffst_plan_s {
   int M = 0, N = 0, j0 = 0, eta = 0, Hc = 0;
+  int variant = 0;                      // FFST_VARIANT_CLASSIC or FFST_VARIANT_SMOOTH
   int hm = 0, hn = 0;
   int device = 0;
   std::vector<ffst::PlaneDesc> planes;  // host copy

@@ -243,6 +243,8 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
   P.win.psi1_row = tab + j0 * (P.hn + 1);
   P.win.phi_col = P.win.psi1_row + j0 * (P.hm + 1);
   P.win.phi_row = P.win.phi_col + (P.hn + 1);
+  P.win.smooth = 0;  // the classic construction only
+  P.win.sig_col = P.win.sig_row = P.win.alp_col = P.win.alp_row = nullptr;
 
   NaSetup su;
   su.M = rows;

@@ -43,6 +43,18 @@ static double varphi64(double w) {
   return 0.0;
 }
 
+// 1 - varphi(w)^2, written as a sine square so it keeps full precision
+// where varphi is close to 1.
+static double varphi_sig64(double w) {
+  w = std::fabs(w);
+  if (w <= 0.5) return 0.0;
+  if (w < 1.0) {
+    const double s = std::sin(0.5 * kPi * v64(2.0 * w - 1.0));
+    return s * s;
+  }
+  return 1.0;
+}
+
 // ---------------------------------------------------------------------------
 // device kernels used at plan time / for export
 // ---------------------------------------------------------------------------
@@ -371,8 +383,14 @@ static cudaError_t upload(float2** dst, const std::vector<float2>& v) {
 using namespace ffst;
 
 extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* out) {
+  return ffst_plan_variant(rows, cols, scales, FFST_VARIANT_CLASSIC, out);
+}
+
+extern "C" ffst_status ffst_plan_variant(int rows, int cols, int scales, int variant, ffst_plan_t* out) {
   if (!out) return fail(FFST_ERR_INVALID_ARG, "ffst_plan: out is NULL");
   *out = nullptr;
+  if (variant != FFST_VARIANT_CLASSIC && variant != FFST_VARIANT_SMOOTH)
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_variant: variant must be FFST_VARIANT_CLASSIC or FFST_VARIANT_SMOOTH");
   if (rows < 8 || cols < 8 || rows > 4096 || cols > 4096 || rows % 2 || cols % 2 || !supported_line(rows) ||
       !supported_line(cols / 2))
     return fail(FFST_ERR_UNSUPPORTED_SIZE,
@@ -395,6 +413,7 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
   p->Hc = cols / 2 + 1;
   p->hm = rows / 2;
   p->hn = cols / 2;
+  p->variant = variant;
 
   // plane table, Sec. 3.5.2: low-pass, then per scale counter-clockwise
   p->planes.clear();
@@ -421,15 +440,32 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
   const double X = std::ldexp(1.0, 2 * j0 - 1);
   const double dc = X / p->hn, dr = X / p->hm;
   const int ncol = p->hn + 1, nrow = p->hm + 1;
-  std::vector<float> tab((size_t)j0 * ncol + (size_t)j0 * nrow + ncol + nrow);
+  // layout: psi1 col [j0][ncol] | psi1 row [j0][nrow] | phi col | phi row |
+  //         smooth: sig col [j0][ncol] | sig row [j0][nrow] | alp col [j0][ncol] | alp row [j0][nrow]
+  const size_t per_scale = (size_t)j0 * (ncol + nrow);
+  std::vector<float> tab(per_scale + ncol + nrow + 2 * per_scale);
   float* psi1_col = tab.data();
   float* psi1_row = psi1_col + (size_t)j0 * ncol;
   float* phi_col = psi1_row + (size_t)j0 * nrow;
   float* phi_row = phi_col + ncol;
+  float* sig_col = phi_row + nrow;
+  float* sig_row = sig_col + (size_t)j0 * ncol;
+  float* alp_col = sig_row + (size_t)j0 * nrow;
+  float* alp_row = alp_col + (size_t)j0 * ncol;
   for (int j = 0; j < j0; ++j) {
     const double a = std::ldexp(1.0, -2 * j);  // a_j = 4^-j
-    for (int q = 0; q < ncol; ++q) psi1_col[(size_t)j * ncol + q] = (float)psi1_64(a * q * dc);
-    for (int q = 0; q < nrow; ++q) psi1_row[(size_t)j * nrow + q] = (float)psi1_64(a * q * dr);
+    for (int q = 0; q < ncol; ++q) {
+      psi1_col[(size_t)j * ncol + q] = (float)psi1_64(a * q * dc);
+      sig_col[(size_t)j * ncol + q] = (float)varphi_sig64(a * q * dc);
+      const double f = varphi64(0.25 * a * q * dc);
+      alp_col[(size_t)j * ncol + q] = (float)(f * f);
+    }
+    for (int q = 0; q < nrow; ++q) {
+      psi1_row[(size_t)j * nrow + q] = (float)psi1_64(a * q * dr);
+      sig_row[(size_t)j * nrow + q] = (float)varphi_sig64(a * q * dr);
+      const double f = varphi64(0.25 * a * q * dr);
+      alp_row[(size_t)j * nrow + q] = (float)(f * f);
+    }
   }
   for (int q = 0; q < ncol; ++q) phi_col[q] = (float)varphi64(q * dc);
   for (int q = 0; q < nrow; ++q) phi_row[q] = (float)varphi64(q * dr);
@@ -446,6 +482,11 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
   p->win.psi1_row = p->d_tables + (size_t)j0 * ncol;
   p->win.phi_col = p->win.psi1_row + (size_t)j0 * nrow;
   p->win.phi_row = p->win.phi_col + ncol;
+  p->win.smooth = variant == FFST_VARIANT_SMOOTH;
+  p->win.sig_col = p->win.phi_row + nrow;
+  p->win.sig_row = p->win.sig_col + (size_t)j0 * ncol;
+  p->win.alp_col = p->win.sig_row + (size_t)j0 * nrow;
+  p->win.alp_row = p->win.alp_col + (size_t)j0 * ncol;
 
   // twiddles (FP64 -> FP32): row lines of length N/2, their real split, column lines of length M
   if ((e = upload(&p->d_tw_rows, pass_table(cols / 2, row_E(cols / 2)))) != cudaSuccess) return cuda_fail(e, "twiddles");

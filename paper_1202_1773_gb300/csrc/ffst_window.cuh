@@ -2,6 +2,8 @@
 //
 // Definitions (arXiv:1202.1773):
 //   v          Sec. 2.1 eq. (v)      polynomial piece p(x) = x^4 (35 - 84x + 70x^2 - 20x^3)
+//   smooth     Sec. 3.4 eqs. (newPsi1), (smoothPsi) and Sec. 2.4 eq. (Phi): a
+//              2-D radial factor for both cones, tensor low-pass
 //   psi2_hat   Sec. 2.1 eq. (Psi2)   sqrt(v(1 - |u|)), zero for |u| >= 1
 //   psi1_hat   Sec. 2.1 eq. (Psi1)   per-scale 1-D table, FP64-generated on the host
 //   varphi     Sec. 2.4              1-D table, FP64-generated on the host
@@ -34,6 +36,26 @@ __device__ __forceinline__ float psi2_hat(float u) {
   return sqrtf(vv);
 }
 
+// Radial factor of the smooth shearlets of scale j (Sec. 3.4 eq. newPsi1):
+// Psi1(w) = sqrt(Phi(w/4)^2 - Phi(w)^2), Phi = varphi x varphi, at
+// w = 4^-j xi.  Where both |w_i| <= 2, Phi(w/4) = 1 and the difference is
+// 1 - (1 - s1)(1 - s2) = s1 + s2 - s1 s2 with s = 1 - varphi(w)^2 read from a
+// table generated in FP64 (no cancellation near the inner edge); elsewhere
+// varphi(w) = 0 on the axis beyond 2 and the difference is Phi(w/4)^2.
+__device__ __forceinline__ float smooth_radial(const WinParams& w, int j, int a1, int a2) {
+  const float ac = __ldg(&w.alp_col[j * (w.hn + 1) + a1]);
+  const float ar = __ldg(&w.alp_row[j * (w.hm + 1) + a2]);
+  float r2;
+  if (ac == 1.0f && ar == 1.0f) {
+    const float sc = __ldg(&w.sig_col[j * (w.hn + 1) + a1]);
+    const float sr = __ldg(&w.sig_row[j * (w.hm + 1) + a2]);
+    r2 = fmaf(-sc, sr, sc + sr);
+  } else {
+    r2 = ac * ar;
+  }
+  return sqrtf(r2);
+}
+
 // Unfixed spectrum of plane (kappa, j, k) at integer frequency (o2, o1).
 // |o1| <= floor(N/2), |o2| <= floor(M/2), M, N <= 4096 and j <= 7 keep every
 // product below 2^31.
@@ -41,7 +63,10 @@ __device__ __forceinline__ float win_raw(const WinParams& w, int kappa, int j, i
   const int a2 = abs(o2), a1 = abs(o1);
   const int lhs = a2 * w.hn;  // |xi2| ~ lhs, |xi1| ~ rhs (common factor X/(hm hn))
   const int rhs = a1 * w.hm;
-  if (kappa == kLowpass) return (lhs <= rhs) ? __ldg(&w.phi_col[a1]) : __ldg(&w.phi_row[a2]);
+  if (kappa == kLowpass) {
+    if (w.smooth) return __ldg(&w.phi_col[a1]) * __ldg(&w.phi_row[a2]);  // Sec. 2.4 eq. (Phi)
+    return (lhs <= rhs) ? __ldg(&w.phi_col[a1]) : __ldg(&w.phi_row[a2]);
+  }
   bool use_h;
   if (lhs < rhs) {
     use_h = true;
@@ -56,14 +81,15 @@ __device__ __forceinline__ float win_raw(const WinParams& w, int kappa, int j, i
   float p1;
   int num, den;
   if (use_h) {
-    p1 = __ldg(&w.psi1_col[j * (w.hn + 1) + a1]);
+    p1 = w.smooth ? 0.0f : __ldg(&w.psi1_col[j * (w.hn + 1) + a1]);
     num = (1 << j) * o2 * w.hn + k * o1 * w.hm;
     den = o1 * w.hm;
   } else {
-    p1 = __ldg(&w.psi1_row[j * (w.hm + 1) + a2]);
+    p1 = w.smooth ? 0.0f : __ldg(&w.psi1_row[j * (w.hm + 1) + a2]);
     num = (1 << j) * o1 * w.hm + k * o2 * w.hn;
     den = o2 * w.hn;
   }
+  if (w.smooth) p1 = smooth_radial(w, j, a1, a2);  // both cones (Sec. 3.4 eq. smoothPsi)
   if (p1 == 0.0f) return 0.0f;
   const float u = __int2float_rn(num) / __int2float_rn(den);
   return p1 * psi2_hat(u);
