@@ -53,70 +53,111 @@ import numpy as np
 # ---------------------------------------------------------------------------
 
 
-def v(x):
-    """Meyer auxiliary function, Sec. 2.1 eq. (v).
+def _v_poly_coeffs(k: int):
+    """Coefficients a_n of v(x) = sum_n a_n x^n on [0, 1] for v'(x) = c x^k (x-1)^k, v(1) = 1
+    (Sec. 3.4 remark construction_v): the binomial expansion of x^k (x-1)^k integrated
+    term by term, c = (-1)^k (2k+1)! / (k!)^2 (a Beta integral)."""
+    from math import comb, factorial
 
-    0 for x < 0, 35x^4 - 84x^5 + 70x^6 - 20x^7 on [0, 1], 1 for x > 1.
+    c = (-1) ** k * factorial(2 * k + 1) / factorial(k) ** 2
+    a = np.zeros(2 * k + 2)
+    for m in range(k + 1):
+        a[k + m + 1] = c * comb(k, m) * (-1) ** (k - m) / (k + m + 1)
+    return a
+
+
+def v(x, vfun="meyer"):
+    """Auxiliary function v, Sec. 2.1 eq. (v) and its variants (Sec. 2.1, Sec. 3.4
+    remark construction_v); 0 for x < 0 and 1 for x > 1 in every variant.
+
+    * "meyer": 35x^4 - 84x^5 + 70x^6 - 20x^7 on [0, 1] (the paper's choice);
+    * "quadratic": 2x^2 on [0, 1/2], 1 - 2(1 - x)^2 on [1/2, 1] (Sec. 2.1, the
+      simpler choice the paper quotes);
+    * ("poly", k): v'(x) = c x^k (x - 1)^k, v(1) = 1 (C^k shearlets; k = 3 is "meyer");
+    * "cinf": s(x-1) / (s(x-1) + s(x)), s(x) = exp(-(1/(1+x)^2 + 1/(1-x)^2)) (C^infinity).
     """
     x = np.asarray(x, dtype=np.float64)
-    # the same polynomial in nested (Horner) form, which rounds less near x = 1
-    poly = x**4 * (35.0 + x * (-84.0 + x * (70.0 - 20.0 * x)))
+    if vfun == "meyer":
+        # the polynomial in nested (Horner) form, which rounds less near x = 1
+        poly = x**4 * (35.0 + x * (-84.0 + x * (70.0 - 20.0 * x)))
+    elif vfun == "quadratic":
+        poly = np.where(x <= 0.5, 2.0 * x * x, 1.0 - 2.0 * (1.0 - x) ** 2)
+    elif isinstance(vfun, tuple) and vfun[0] == "poly":
+        # Horner on [0, 1/2] and the symmetry v(x) = 1 - v(1 - x) above it,
+        # which keeps the high-degree cancellation near x = 1 out
+        a = _v_poly_coeffs(int(vfun[1]))
+
+        def horner(y):
+            out = np.zeros_like(y)
+            for coef in a[::-1]:
+                out = out * y + coef
+            return out
+
+        poly = np.where(x <= 0.5, horner(x), 1.0 - horner(1.0 - x))
+    elif vfun == "cinf":
+        with np.errstate(divide="ignore", over="ignore", invalid="ignore"):
+            s0 = np.exp(-(1.0 / x**2 + 1.0 / (2.0 - x) ** 2))          # s(x - 1)
+            s1 = np.exp(-(1.0 / (1.0 + x) ** 2 + 1.0 / (1.0 - x) ** 2))  # s(x)
+            poly = s0 / (s0 + s1)
+        poly = np.where(x <= 0.0, 0.0, np.where(x >= 1.0, 1.0, poly))
+    else:
+        raise ValueError(f"unknown v variant {vfun!r}")
     return np.where(x < 0.0, 0.0, np.where(x > 1.0, 1.0, poly))
 
 
-def b(omega):
+def b(omega, vfun="meyer"):
     """Bump b(omega), Sec. 2.1 eq. (b): supported on 1 <= |omega| <= 4."""
     w = np.abs(np.asarray(omega, dtype=np.float64))
-    rise = np.sin(0.5 * np.pi * v(w - 1.0))
-    fall = np.cos(0.5 * np.pi * v(0.5 * w - 1.0))
+    rise = np.sin(0.5 * np.pi * v(w - 1.0, vfun))
+    fall = np.cos(0.5 * np.pi * v(0.5 * w - 1.0, vfun))
     return np.where((w >= 1.0) & (w <= 2.0), rise,
                     np.where((w > 2.0) & (w <= 4.0), fall, 0.0))
 
 
-def psi1_hat(omega):
+def psi1_hat(omega, vfun="meyer"):
     """Radial (scale) window, Sec. 2.1 eq. (Psi1): sqrt(b(2w)^2 + b(w)^2)."""
-    return np.sqrt(b(2.0 * np.asarray(omega, dtype=np.float64)) ** 2 + b(omega) ** 2)
+    return np.sqrt(b(2.0 * np.asarray(omega, dtype=np.float64), vfun) ** 2 + b(omega, vfun) ** 2)
 
 
-def psi2_hat(omega):
+def psi2_hat(omega, vfun="meyer"):
     """Directional window, Sec. 2.1 eq. (Psi2).
 
     sqrt(v(1 + w)) for w <= 0 and sqrt(v(1 - w)) for w > 0.
     """
     w = np.asarray(omega, dtype=np.float64)
-    return np.where(w <= 0.0, np.sqrt(v(1.0 + w)), np.sqrt(v(1.0 - w)))
+    return np.where(w <= 0.0, np.sqrt(v(1.0 + w, vfun)), np.sqrt(v(1.0 - w, vfun)))
 
 
-def varphi(omega):
+def varphi(omega, vfun="meyer"):
     """1-D scaling window of Sec. 2.4 (the function written varphi there)."""
     w = np.abs(np.asarray(omega, dtype=np.float64))
-    mid = np.cos(0.5 * np.pi * v(2.0 * w - 1.0))
+    mid = np.cos(0.5 * np.pi * v(2.0 * w - 1.0, vfun))
     return np.where(w <= 0.5, 1.0, np.where(w < 1.0, mid, 0.0))
 
 
-def Phi_hat(w1, w2):
+def Phi_hat(w1, w2, vfun="meyer"):
     """Tensor-product scaling function varphi(w1) varphi(w2), Sec. 2.4 eq. (Phi)."""
-    return varphi(w1) * varphi(w2)
+    return varphi(w1, vfun) * varphi(w2, vfun)
 
 
-def Psi1_hat(w1, w2):
+def Psi1_hat(w1, w2, vfun="meyer"):
     """2-D radial window of the smooth shearlets, Sec. 3.4 eq. (newPsi1):
     sqrt(Phi_hat(w/4)^2 - Phi_hat(w)^2); supported in [-4, 4]^2 minus
     [-1/2, 1/2]^2."""
     w1 = np.asarray(w1, dtype=np.float64)
     w2 = np.asarray(w2, dtype=np.float64)
-    d = Phi_hat(0.25 * w1, 0.25 * w2) ** 2 - Phi_hat(w1, w2) ** 2
+    d = Phi_hat(0.25 * w1, 0.25 * w2, vfun) ** 2 - Phi_hat(w1, w2, vfun) ** 2
     return np.sqrt(np.maximum(d, 0.0))
 
 
-def phi_hat(xi1, xi2):
+def phi_hat(xi1, xi2, vfun="meyer"):
     """Cone-adapted scaling function, Sec. 2.4 eq. (phi).
 
     varphi(xi1) where |xi2| <= |xi1|, varphi(xi2) where |xi1| < |xi2|.
     """
     xi1 = np.asarray(xi1, dtype=np.float64)
     xi2 = np.asarray(xi2, dtype=np.float64)
-    return np.where(np.abs(xi2) <= np.abs(xi1), varphi(xi1), varphi(xi2))
+    return np.where(np.abs(xi2) <= np.abs(xi1), varphi(xi1, vfun), varphi(xi2, vfun))
 
 
 # ---------------------------------------------------------------------------
@@ -229,7 +270,7 @@ def _ratio(num, den, mask):
     return out
 
 
-def spectrum_raw(rows: int, cols: int, scales: int, i: int, smooth: bool = False) -> np.ndarray:
+def spectrum_raw(rows: int, cols: int, scales: int, i: int, smooth: bool = False, vfun="meyer") -> np.ndarray:
     """Spectrum of plane i on Xi without the Nyquist fix, FFT storage order.
 
     Sec. 3.1 eq. (shearletTransform):
@@ -240,22 +281,23 @@ def spectrum_raw(rows: int, cols: int, scales: int, i: int, smooth: bool = False
                   C^h and on the seam lines, the v formula on C^v.
     smooth=True gives the smooth shearlets of Sec. 3.4 eq. (smoothPsi): the
     radial factor of both cones is Psi1_hat(4^-j xi) (eq. newPsi1) and the
-    low-pass is the tensor product Phi_hat(xi) (Sec. 2.4 eq. Phi).
+    low-pass is the tensor product Phi_hat(xi) (Sec. 2.4 eq. Phi).  vfun
+    selects the auxiliary function v of every window (see ``v``).
     """
     kappa, j, k = plane_table(scales)[i]
     o1, o2, xi1, xi2 = grid(rows, cols, scales)
     if kappa == "lowpass":
-        return Phi_hat(xi1, xi2) if smooth else phi_hat(xi1, xi2)
+        return Phi_hat(xi1, xi2, vfun) if smooth else phi_hat(xi1, xi2, vfun)
     ch, cv, cx = cones(rows, cols, o1, o2)
     a = 4.0 ** (-j)
     J = 2.0**j
     if smooth:
-        r = Psi1_hat(a * xi1, a * xi2)
-        h_part = r * psi2_hat(J * _ratio(xi2, xi1, xi1 != 0) + k)
-        v_part = r * psi2_hat(J * _ratio(xi1, xi2, xi2 != 0) + k)
+        r = Psi1_hat(a * xi1, a * xi2, vfun)
+        h_part = r * psi2_hat(J * _ratio(xi2, xi1, xi1 != 0) + k, vfun)
+        v_part = r * psi2_hat(J * _ratio(xi1, xi2, xi2 != 0) + k, vfun)
     else:
-        h_part = psi1_hat(a * xi1) * psi2_hat(J * _ratio(xi2, xi1, xi1 != 0) + k)
-        v_part = psi1_hat(a * xi2) * psi2_hat(J * _ratio(xi1, xi2, xi2 != 0) + k)
+        h_part = psi1_hat(a * xi1, vfun) * psi2_hat(J * _ratio(xi2, xi1, xi1 != 0) + k, vfun)
+        v_part = psi1_hat(a * xi2, vfun) * psi2_hat(J * _ratio(xi1, xi2, xi2 != 0) + k, vfun)
     if kappa == "h":
         return np.where(ch, h_part, 0.0)
     if kappa == "v":
@@ -288,32 +330,33 @@ def nyquist_mirror(psi: np.ndarray) -> np.ndarray:
     return out
 
 
-def spectrum(rows: int, cols: int, scales: int, i: int, real_fix: bool = True, smooth: bool = False) -> np.ndarray:
+def spectrum(rows: int, cols: int, scales: int, i: int, real_fix: bool = True, smooth: bool = False,
+             vfun="meyer") -> np.ndarray:
     """Spectrum psi_hat_i of plane i (FFT storage order), fix applied by default.
 
     The fix is on by default, as the paper's ``realReal`` option (Sec. 3.5.3).
     """
-    raw = spectrum_raw(rows, cols, scales, i, smooth)
+    raw = spectrum_raw(rows, cols, scales, i, smooth, vfun)
     return nyquist_mirror(raw) if real_fix else raw
 
 
 def spectra(rows: int, cols: int, scales: int | None = None, real_fix: bool = True,
-            smooth: bool = False) -> np.ndarray:
+            smooth: bool = False, vfun="meyer") -> np.ndarray:
     """Stack of all eta spectra, shape (eta, M, N), Sec. 3.5.2."""
     if scales is None:
         scales = default_scales(rows, cols)
-    return np.stack([spectrum(rows, cols, scales, i, real_fix, smooth)
+    return np.stack([spectrum(rows, cols, scales, i, real_fix, smooth, vfun)
                      for i in range(num_planes(scales))])
 
 
 def frame_sum(rows: int, cols: int, scales: int | None = None, real_fix: bool = True,
-              smooth: bool = False) -> np.ndarray:
+              smooth: bool = False, vfun="meyer") -> np.ndarray:
     """sum_i psi_hat_i^2 on the grid (Sec. 3.6, frame tightness)."""
     if scales is None:
         scales = default_scales(rows, cols)
     acc = np.zeros((rows, cols))
     for i in range(num_planes(scales)):
-        acc += spectrum(rows, cols, scales, i, real_fix, smooth) ** 2
+        acc += spectrum(rows, cols, scales, i, real_fix, smooth, vfun) ** 2
     return acc
 
 
@@ -333,13 +376,13 @@ def forward_complex(f: np.ndarray, scales: int | None = None, real_fix: bool = T
                      for i in range(num_planes(scales))])
 
 
-def forward_plane(F: np.ndarray, scales: int, i: int, smooth: bool = False) -> np.ndarray:
+def forward_plane(F: np.ndarray, scales: int, i: int, smooth: bool = False, vfun="meyer") -> np.ndarray:
     """One real coefficient plane from a precomputed F = fft2(f)."""
     M, N = F.shape
-    return np.real(np.fft.ifft2(spectrum(M, N, scales, i, smooth=smooth) * F))
+    return np.real(np.fft.ifft2(spectrum(M, N, scales, i, smooth=smooth, vfun=vfun) * F))
 
 
-def forward(f: np.ndarray, scales: int | None = None, smooth: bool = False) -> np.ndarray:
+def forward(f: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer") -> np.ndarray:
     """Real coefficient stack (eta, M, N): the real part of ``forward_complex``.
 
     With the Nyquist fix the imaginary part is rounding noise (Sec. 3.8.1).
@@ -349,10 +392,10 @@ def forward(f: np.ndarray, scales: int | None = None, smooth: bool = False) -> n
     if scales is None:
         scales = default_scales(M, N)
     F = np.fft.fft2(f)
-    return np.stack([forward_plane(F, scales, i, smooth) for i in range(num_planes(scales))])
+    return np.stack([forward_plane(F, scales, i, smooth, vfun) for i in range(num_planes(scales))])
 
 
-def adjoint(c: np.ndarray, scales: int | None = None, smooth: bool = False) -> np.ndarray:
+def adjoint(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer") -> np.ndarray:
     """T* c = Re ifft2( sum_i psi_hat_i * fft2(c_i) ), Sec. 3.3.
 
     For a Parseval frame T* = T^-1 (Sec. 3.2, eq. shearlet_transform_as_matrix).
@@ -363,11 +406,11 @@ def adjoint(c: np.ndarray, scales: int | None = None, smooth: bool = False) -> n
         scales = default_scales(M, N)
     acc = np.zeros((M, N), dtype=np.complex128)
     for i in range(num_planes(scales)):
-        acc += spectrum(M, N, scales, i, smooth=smooth) * np.fft.fft2(c[i])
+        acc += spectrum(M, N, scales, i, smooth=smooth, vfun=vfun) * np.fft.fft2(c[i])
     return np.real(np.fft.ifft2(acc))
 
 
-def inverse(c: np.ndarray, scales: int | None = None, smooth: bool = False) -> np.ndarray:
+def inverse(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer") -> np.ndarray:
     """Re ifft2( sum_i psi_hat_i * fft2(c_i) / sum_i psi_hat_i^2 ), Sec. 3.3.
 
     Sec. 3.3 eq. (inverseShearletTransform) sums the products; the division
@@ -381,7 +424,7 @@ def inverse(c: np.ndarray, scales: int | None = None, smooth: bool = False) -> n
     acc = np.zeros((M, N), dtype=np.complex128)
     den = np.zeros((M, N))
     for i in range(num_planes(scales)):
-        s = spectrum(M, N, scales, i, smooth=smooth)
+        s = spectrum(M, N, scales, i, smooth=smooth, vfun=vfun)
         acc += s * np.fft.fft2(c[i])
         den += s * s
     return np.real(np.fft.ifft2(acc / den))

@@ -105,3 +105,64 @@ def test_seam_shearlet_smooth_across_the_diagonal(c):
         jump[smooth] = abs(float(right - left))
     assert jump[False] > 1e-3
     assert jump[True] < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# variants of the auxiliary function v (Sec. 2.1 and Sec. 3.4 remark construction_v)
+# ---------------------------------------------------------------------------
+
+VFUNS = ["meyer", "quadratic", ("poly", 1), ("poly", 5), "cinf"]
+
+
+def test_v_poly_k3_is_the_paper_polynomial():
+    # v'(x) = c x^3 (x-1)^3 with v(1) = 1 gives c = -140 and eq. (v)
+    np.testing.assert_allclose(o._v_poly_coeffs(3), [0, 0, 0, 0, 35, -84, 70, -20], atol=1e-12)
+    x = np.linspace(-0.2, 1.2, 57)
+    np.testing.assert_allclose(o.v(x, ("poly", 3)), o.v(x), atol=2e-15)
+
+
+def test_v_quadratic_closed_form():
+    # the piecewise quadratic quoted in Sec. 2.1
+    np.testing.assert_allclose(o.v([0.25, 0.5, 0.75], "quadratic"), [0.125, 0.5, 0.875], atol=0)
+
+
+@pytest.mark.parametrize("vfun", VFUNS)
+def test_v_variant_shape(vfun):
+    x = np.linspace(0.0, 1.0, 201)
+    y = o.v(x, vfun)
+    assert y[0] == 0.0 and y[-1] == 1.0
+    assert np.all(np.diff(y) >= -1e-15)  # nondecreasing
+    np.testing.assert_allclose(y + o.v(1.0 - x, vfun), 1.0, atol=1e-14)  # symmetry around (1/2, 1/2)
+    assert np.all(o.v(np.array([-1.0, -1e-9]), vfun) == 0.0) and np.all(o.v(np.array([1 + 1e-9, 3.0]), vfun) == 1.0)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_v_poly_flatness_order(k):
+    # v^{(n)}(0) = 0 for 1 <= n <= k (C^k shearlets, Sec. 3.4): v(h) = O(h^{k+1}) and the
+    # Taylor coefficient of order k+1 is c/(k+1) with c = (-1)^k (2k+1)!/(k!)^2
+    from math import factorial
+
+    c = (-1) ** k * factorial(2 * k + 1) / factorial(k) ** 2
+    for h in (1e-2, 5e-3):
+        assert o.v(h, ("poly", k)) == pytest.approx(abs(c) / (k + 1) * h ** (k + 1), rel=0.1)
+
+
+def test_v_cinf_flat_at_the_ends():
+    # every derivative vanishes at 0 and 1: v(h) decays faster than any power
+    for h in (0.05, 0.02):
+        assert o.v(h, "cinf") < h**8
+        assert 1.0 - o.v(1.0 - h, "cinf") < h**8
+
+
+@pytest.mark.parametrize("vfun", VFUNS)
+@pytest.mark.parametrize("smooth", [False, True])
+def test_v_variant_frames_are_tight(vfun, smooth):
+    # any v with v(x) + v(1-x) = 1 keeps both partitions of unity, hence a Parseval frame
+    assert np.abs(o.frame_sum(64, 64, 3, smooth=smooth, vfun=vfun) - 1.0).max() <= 1e-14
+    assert np.abs(o.frame_sum(128, 96, 3, smooth=smooth, vfun=vfun) - 1.0).max() <= 1e-14
+
+
+def test_v_variants_change_the_spectra():
+    base = o.spectra(32, 32, 2)
+    for vfun in VFUNS[1:]:
+        assert np.abs(o.spectra(32, 32, 2, vfun=vfun) - base).max() > 1e-3
