@@ -218,29 +218,34 @@ def freq_index(L: int) -> np.ndarray:
     return np.where(p < half, p, p - L)
 
 
-def grid_spacing(L: int, scales: int) -> float:
-    """Grid step of one axis of Xi, Sec. 3.5.1: X / floor(L/2), X = 2^{2 j0 - 1}.
+def grid_spacing(L: int, scales: int, max_scale: str = "max") -> float:
+    """Grid step of one axis of Xi, Sec. 3.5.1: X / floor(L/2).
 
+    X = 2^{2 j0 - 1} (the paper's choice X_3, the largest finest scale, its
+    option maxScale = 'max') or X = 2^{2 j0 - 2} (X_2, the smallest reasonable
+    finest scale, maxScale = 'min'); Sec. 3.5.1 allows any X between the two.
     For odd L the paper's grid is linspace(-X, X, L), step 2X/(L-1) =
     X/floor(L/2); for even L it pads to L+1 and drops the last sample,
     which keeps the same step.
     """
-    X = 2.0 ** (2 * scales - 1)
+    if max_scale not in ("max", "min"):
+        raise ValueError(f"max_scale must be 'max' or 'min', not {max_scale!r}")
+    X = 2.0 ** (2 * scales - (1 if max_scale == "max" else 2))
     h = L // 2
     if h == 0:
         return 0.0
     return X / h
 
 
-def grid(rows: int, cols: int, scales: int):
+def grid(rows: int, cols: int, scales: int, max_scale: str = "max"):
     """Integer indices (o1, o2) and grid points (xi1, xi2), shape (M, N).
 
     xi1 (omega_1) varies along columns, xi2 (omega_2) along rows.
     """
     o1 = freq_index(cols)[None, :] * np.ones((rows, 1), dtype=np.int64)
     o2 = freq_index(rows)[:, None] * np.ones((1, cols), dtype=np.int64)
-    xi1 = o1 * grid_spacing(cols, scales)
-    xi2 = o2 * grid_spacing(rows, scales)
+    xi1 = o1 * grid_spacing(cols, scales, max_scale)
+    xi2 = o2 * grid_spacing(rows, scales, max_scale)
     return o1, o2, xi1, xi2
 
 
@@ -270,7 +275,8 @@ def _ratio(num, den, mask):
     return out
 
 
-def spectrum_raw(rows: int, cols: int, scales: int, i: int, smooth: bool = False, vfun="meyer") -> np.ndarray:
+def spectrum_raw(rows: int, cols: int, scales: int, i: int, smooth: bool = False, vfun="meyer",
+                 max_scale: str = "max") -> np.ndarray:
     """Spectrum of plane i on Xi without the Nyquist fix, FFT storage order.
 
     Sec. 3.1 eq. (shearletTransform):
@@ -282,10 +288,11 @@ def spectrum_raw(rows: int, cols: int, scales: int, i: int, smooth: bool = False
     smooth=True gives the smooth shearlets of Sec. 3.4 eq. (smoothPsi): the
     radial factor of both cones is Psi1_hat(4^-j xi) (eq. newPsi1) and the
     low-pass is the tensor product Phi_hat(xi) (Sec. 2.4 eq. Phi).  vfun
-    selects the auxiliary function v of every window (see ``v``).
+    selects the auxiliary function v of every window (see ``v``), max_scale
+    the grid extent X (see ``grid_spacing``).
     """
     kappa, j, k = plane_table(scales)[i]
-    o1, o2, xi1, xi2 = grid(rows, cols, scales)
+    o1, o2, xi1, xi2 = grid(rows, cols, scales, max_scale)
     if kappa == "lowpass":
         return Phi_hat(xi1, xi2, vfun) if smooth else phi_hat(xi1, xi2, vfun)
     ch, cv, cx = cones(rows, cols, o1, o2)
@@ -331,32 +338,32 @@ def nyquist_mirror(psi: np.ndarray) -> np.ndarray:
 
 
 def spectrum(rows: int, cols: int, scales: int, i: int, real_fix: bool = True, smooth: bool = False,
-             vfun="meyer") -> np.ndarray:
+             vfun="meyer", max_scale: str = "max") -> np.ndarray:
     """Spectrum psi_hat_i of plane i (FFT storage order), fix applied by default.
 
     The fix is on by default, as the paper's ``realReal`` option (Sec. 3.5.3).
     """
-    raw = spectrum_raw(rows, cols, scales, i, smooth, vfun)
+    raw = spectrum_raw(rows, cols, scales, i, smooth, vfun, max_scale)
     return nyquist_mirror(raw) if real_fix else raw
 
 
 def spectra(rows: int, cols: int, scales: int | None = None, real_fix: bool = True,
-            smooth: bool = False, vfun="meyer") -> np.ndarray:
+            smooth: bool = False, vfun="meyer", max_scale: str = "max") -> np.ndarray:
     """Stack of all eta spectra, shape (eta, M, N), Sec. 3.5.2."""
     if scales is None:
         scales = default_scales(rows, cols)
-    return np.stack([spectrum(rows, cols, scales, i, real_fix, smooth, vfun)
+    return np.stack([spectrum(rows, cols, scales, i, real_fix, smooth, vfun, max_scale)
                      for i in range(num_planes(scales))])
 
 
 def frame_sum(rows: int, cols: int, scales: int | None = None, real_fix: bool = True,
-              smooth: bool = False, vfun="meyer") -> np.ndarray:
+              smooth: bool = False, vfun="meyer", max_scale: str = "max") -> np.ndarray:
     """sum_i psi_hat_i^2 on the grid (Sec. 3.6, frame tightness)."""
     if scales is None:
         scales = default_scales(rows, cols)
     acc = np.zeros((rows, cols))
     for i in range(num_planes(scales)):
-        acc += spectrum(rows, cols, scales, i, real_fix, smooth, vfun) ** 2
+        acc += spectrum(rows, cols, scales, i, real_fix, smooth, vfun, max_scale) ** 2
     return acc
 
 
@@ -376,13 +383,15 @@ def forward_complex(f: np.ndarray, scales: int | None = None, real_fix: bool = T
                      for i in range(num_planes(scales))])
 
 
-def forward_plane(F: np.ndarray, scales: int, i: int, smooth: bool = False, vfun="meyer") -> np.ndarray:
+def forward_plane(F: np.ndarray, scales: int, i: int, smooth: bool = False, vfun="meyer",
+                  max_scale: str = "max") -> np.ndarray:
     """One real coefficient plane from a precomputed F = fft2(f)."""
     M, N = F.shape
-    return np.real(np.fft.ifft2(spectrum(M, N, scales, i, smooth=smooth, vfun=vfun) * F))
+    return np.real(np.fft.ifft2(spectrum(M, N, scales, i, smooth=smooth, vfun=vfun, max_scale=max_scale) * F))
 
 
-def forward(f: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer") -> np.ndarray:
+def forward(f: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer",
+            max_scale: str = "max") -> np.ndarray:
     """Real coefficient stack (eta, M, N): the real part of ``forward_complex``.
 
     With the Nyquist fix the imaginary part is rounding noise (Sec. 3.8.1).
@@ -392,10 +401,11 @@ def forward(f: np.ndarray, scales: int | None = None, smooth: bool = False, vfun
     if scales is None:
         scales = default_scales(M, N)
     F = np.fft.fft2(f)
-    return np.stack([forward_plane(F, scales, i, smooth, vfun) for i in range(num_planes(scales))])
+    return np.stack([forward_plane(F, scales, i, smooth, vfun, max_scale) for i in range(num_planes(scales))])
 
 
-def adjoint(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer") -> np.ndarray:
+def adjoint(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer",
+            max_scale: str = "max") -> np.ndarray:
     """T* c = Re ifft2( sum_i psi_hat_i * fft2(c_i) ), Sec. 3.3.
 
     For a Parseval frame T* = T^-1 (Sec. 3.2, eq. shearlet_transform_as_matrix).
@@ -406,11 +416,12 @@ def adjoint(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun
         scales = default_scales(M, N)
     acc = np.zeros((M, N), dtype=np.complex128)
     for i in range(num_planes(scales)):
-        acc += spectrum(M, N, scales, i, smooth=smooth, vfun=vfun) * np.fft.fft2(c[i])
+        acc += spectrum(M, N, scales, i, smooth=smooth, vfun=vfun, max_scale=max_scale) * np.fft.fft2(c[i])
     return np.real(np.fft.ifft2(acc))
 
 
-def inverse(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer") -> np.ndarray:
+def inverse(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer",
+            max_scale: str = "max") -> np.ndarray:
     """Re ifft2( sum_i psi_hat_i * fft2(c_i) / sum_i psi_hat_i^2 ), Sec. 3.3.
 
     Sec. 3.3 eq. (inverseShearletTransform) sums the products; the division
@@ -424,7 +435,7 @@ def inverse(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun
     acc = np.zeros((M, N), dtype=np.complex128)
     den = np.zeros((M, N))
     for i in range(num_planes(scales)):
-        s = spectrum(M, N, scales, i, smooth=smooth, vfun=vfun)
+        s = spectrum(M, N, scales, i, smooth=smooth, vfun=vfun, max_scale=max_scale)
         acc += s * np.fft.fft2(c[i])
         den += s * s
     return np.real(np.fft.ifft2(acc / den))

@@ -203,3 +203,23 @@ def test_transpose_symmetry_square():
         else:
             partner = i
         np.testing.assert_allclose(S[i].T, S[partner], atol=1e-15)
+
+
+def test_max_scale_min_grid():
+    # maxScale = 'min' (Sec. 3.5.3 option, Sec. 3.5.1 choice X_2 = 2^{2 j0 - 2}): half the
+    # extent of the default X_3 = 2^{2 j0 - 1}; both keep the frame tight
+    for n, j0 in ((64, 3), (256, 4)):
+        assert o.grid_spacing(n, j0, "min") * 2 == o.grid_spacing(n, j0)
+        _, _, xi1, _ = o.grid(n, n, j0, "min")
+        assert np.abs(xi1).max() == 2.0 ** (2 * j0 - 2)
+    for smooth in (False, True):
+        assert np.abs(o.frame_sum(64, 64, 3, smooth=smooth, max_scale="min") - 1).max() <= 1e-14
+        assert np.abs(o.frame_sum(96, 128, 3, smooth=smooth, max_scale="min") - 1).max() <= 1e-14
+    # on the smaller grid the finest scale covers less: the finest planes carry
+    # less of the spectrum than with the default extent
+    fine = [i for i, (kap, j, k) in enumerate(o.plane_table(3)) if j == 2]
+    e_max = sum((o.spectrum(64, 64, 3, i) ** 2).sum() for i in fine)
+    e_min = sum((o.spectrum(64, 64, 3, i, max_scale="min") ** 2).sum() for i in fine)
+    assert e_min < e_max
+    with pytest.raises(ValueError):
+        o.grid_spacing(64, 3, "mid")
