@@ -66,10 +66,25 @@ typedef enum {
 /* Plane kinds returned by ffst_plane_index (kappa of Sec. 3.1). */
 enum { FFST_CONE_LOWPASS = 0, FFST_CONE_H = 1, FFST_CONE_V = 2, FFST_CONE_SEAM = 3 };
 
-/* Shearlet constructions (ffst_plan_variant). */
+/* Shearlet constructions (ffst_plan_ex). */
 enum {
   FFST_VARIANT_CLASSIC = 0, /* Sec. 3.1: radial factor psi1 of one axis per cone, cone low-pass  */
   FFST_VARIANT_SMOOTH = 1   /* Sec. 3.4: 2-D radial factor Psi1 (eq. newPsi1), tensor low-pass */
+};
+
+/* Auxiliary function v of every window (ffst_plan_ex); each satisfies
+ * v(x) + v(1 - x) = 1, so every choice keeps the Parseval frame. */
+enum {
+  FFST_V_MEYER = 0,     /* Sec. 2.1 eq. (v): 35x^4 - 84x^5 + 70x^6 - 20x^7 (C^3 shearlets)       */
+  FFST_V_QUADRATIC = 1, /* Sec. 2.1: 2x^2 on [0, 1/2], 1 - 2(1-x)^2 on [1/2, 1]                  */
+  FFST_V_POLY = 2,      /* Sec. 3.4 remark: v' = c x^k (x-1)^k, v(1) = 1, k = vorder in 1..7 (C^k) */
+  FFST_V_CINF = 3       /* Sec. 3.4 remark: s(x-1)/(s(x-1)+s(x)), s(x) = e^{-1/(1+x)^2 - 1/(1-x)^2} */
+};
+
+/* Extent of the frequency grid (ffst_plan_ex), the maxScale option of Sec. 3.5.3. */
+enum {
+  FFST_MAXSCALE_MAX = 0, /* X = 2^{2 j0 - 1} (X_3 of Sec. 3.5.1: the largest finest scale)  */
+  FFST_MAXSCALE_MIN = 1  /* X = 2^{2 j0 - 2} (X_2 of Sec. 3.5.1: the smallest finest scale) */
 };
 
 /*
@@ -83,16 +98,23 @@ enum {
 ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* out);
 
 /*
- * As ffst_plan, for the shearlet construction `variant`: FFST_VARIANT_CLASSIC
- * (what ffst_plan builds) or FFST_VARIANT_SMOOTH, the smooth shearlets of
- * Sec. 3.4 eqs. (newPsi1), (smoothPsi): every plane's radial factor is
- * Psi1(4^-j xi) = sqrt(Phi(4^-j xi / 4)^2 - Phi(4^-j xi)^2) with the tensor
- * scaling function Phi = varphi x varphi of Sec. 2.4 eq. (Phi), which is
- * also the low-pass.  Same planes, order and Parseval property; every
- * transform entry point works on either.  FFST_ERR_INVALID_ARG for another
- * variant code.
+ * As ffst_plan, with the paper's construction options:
+ *   variant    FFST_VARIANT_CLASSIC (what ffst_plan builds) or
+ *              FFST_VARIANT_SMOOTH, the smooth shearlets of Sec. 3.4 eqs.
+ *              (newPsi1), (smoothPsi): every plane's radial factor is
+ *              Psi1(4^-j xi) = sqrt(Phi(4^-j xi / 4)^2 - Phi(4^-j xi)^2) with
+ *              the tensor scaling function Phi = varphi x varphi of Sec. 2.4
+ *              eq. (Phi), which is also the low-pass;
+ *   vfun       the auxiliary function v (FFST_V_*), vorder its order k for
+ *              FFST_V_POLY (ignored otherwise);
+ *   max_scale  FFST_MAXSCALE_MAX (X = 2^{2 j0 - 1}, what ffst_plan builds) or
+ *              FFST_MAXSCALE_MIN (X = 2^{2 j0 - 2}).
+ * Same planes, order and Parseval property; every transform entry point works
+ * on any combination.  FFST_ERR_INVALID_ARG for codes outside these sets or
+ * vorder outside 1..7 with FFST_V_POLY.
  */
-ffst_status ffst_plan_variant(int rows, int cols, int scales, int variant, ffst_plan_t* out);
+ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant, int vfun, int vorder, int max_scale,
+                         ffst_plan_t* out);
 
 /* Query a plan.  Any output pointer may be NULL. */
 ffst_status ffst_plan_info(ffst_plan_t plan, int* rows, int* cols, int* scales, int* num_planes);

@@ -81,15 +81,31 @@ def _storage_of(dtype) -> int:
 class Plan:
     """A libffst plan for rows x cols float32 images on one CUDA device.
 
-    smooth=True builds the smooth shearlets of Sec. 3.4 (ffst_plan_variant).
+    Construction options (ffst_plan_ex): smooth=True builds the smooth
+    shearlets of Sec. 3.4; vfun picks the auxiliary function v ("meyer",
+    "quadratic", ("poly", k) or "cinf"); max_scale="min" uses the smaller
+    grid extent X = 2^{2 j0 - 2}.
     """
 
-    def __init__(self, rows: int, cols: int, scales: int = 0, device=None, smooth: bool = False):
+    _VFUNS = {"meyer": _lib.FFST_V_MEYER, "quadratic": _lib.FFST_V_QUADRATIC, "cinf": _lib.FFST_V_CINF}
+
+    def __init__(self, rows: int, cols: int, scales: int = 0, device=None, smooth: bool = False, vfun="meyer",
+                 max_scale: str = "max"):
         torch = _torch()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.smooth = bool(smooth)
+        if isinstance(vfun, tuple) and len(vfun) == 2 and vfun[0] == "poly":
+            vcode, vorder = _lib.FFST_V_POLY, int(vfun[1])
+        elif vfun in self._VFUNS:
+            vcode, vorder = self._VFUNS[vfun], 0
+        else:
+            raise ValueError(f"unknown vfun {vfun!r}")
+        if max_scale not in ("max", "min"):
+            raise ValueError(f"max_scale must be 'max' or 'min', not {max_scale!r}")
         with torch.cuda.device(self.device):
-            self.handle = ffst_plan(rows, cols, scales, _lib.FFST_VARIANT_SMOOTH if smooth else _lib.FFST_VARIANT_CLASSIC)
+            self.handle = ffst_plan(rows, cols, scales,
+                                    _lib.FFST_VARIANT_SMOOTH if smooth else _lib.FFST_VARIANT_CLASSIC, vcode, vorder,
+                                    _lib.FFST_MAXSCALE_MIN if max_scale == "min" else _lib.FFST_MAXSCALE_MAX)
         self.rows, self.cols, self.scales, self.num_planes = ffst_plan_info(self.handle)
 
     # -- bookkeeping ----------------------------------------------------------

@@ -175,6 +175,11 @@ struct WinParams {
   const float* psi1_row;  // [j0][hm+1]: psi1(4^-j * a * dr), a = |omega_2|
   const float* phi_col;   // [hn+1]:     varphi(a * dc)
   const float* phi_row;   // [hm+1]:     varphi(a * dr)
+  // auxiliary function v of psi2 (Sec. 2.1, Sec. 3.4 remark construction_v):
+  // FFST_V_MEYER, FFST_V_QUADRATIC, FFST_V_POLY (coefficients vc[0..vdeg]
+  // of v on [0, 1/2]) or FFST_V_CINF
+  int vkind, vdeg;
+  float vc[16];
   // smooth shearlets (Sec. 3.4): per scale j, with w = 4^-j a d (d = dc or dr)
   int smooth;
   const float* sig_col;   // [j0][hn+1]: 1 - varphi(w)^2

@@ -243,7 +243,9 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
   P.win.psi1_row = tab + j0 * (P.hn + 1);
   P.win.phi_col = P.win.psi1_row + j0 * (P.hm + 1);
   P.win.phi_row = P.win.phi_col + (P.hn + 1);
-  P.win.smooth = 0;  // the classic construction only
+  P.win.smooth = 0;  // the classic construction, eq. (v), X = 2^{2 j0 - 1} only
+  P.win.vkind = FFST_V_MEYER;
+  P.win.vdeg = 0;
   P.win.sig_col = P.win.sig_row = P.win.alp_col = P.win.alp_row = nullptr;
 
   NaSetup su;

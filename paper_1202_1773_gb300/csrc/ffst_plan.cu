@@ -14,42 +14,85 @@ namespace ffst {
 // ---------------------------------------------------------------------------
 // FP64 window functions for the once-per-plan tables (host only)
 // ---------------------------------------------------------------------------
-// v of Sec. 2.1 eq. (v); the half x > 1/2 uses v(x) = 1 - v(1 - x) (Lemma, Sec. 2.1).
-static double v64(double x) {
+// The plan's auxiliary function v: eq. (v) of Sec. 2.1 or one of its
+// variants (Sec. 2.1, Sec. 3.4 remark construction_v).
+struct VSpec {
+  int kind = FFST_V_MEYER;
+  int deg = 0;     // FFST_V_POLY: degree of v on [0, 1] (2k + 1)
+  double c[16]{};  // FFST_V_POLY: coefficients of v on [0, 1]
+};
+// v'(x) = c x^k (x - 1)^k, v(1) = 1: the binomial expansion integrated term
+// by term, c = (-1)^k (2k + 1)! / (k!)^2.
+static VSpec v_poly_spec(int k) {
+  VSpec s;
+  s.kind = FFST_V_POLY;
+  s.deg = 2 * k + 1;
+  double c = (k % 2 ? -1.0 : 1.0);
+  for (int q = k + 2; q <= 2 * k + 1; ++q) c *= q;  // (2k+1)!/(k+1)! ...
+  for (int q = 2; q <= k; ++q) c /= q;               // ... / k! = (2k+1)!/(k! k!) with the (k+1) below
+  c *= (k + 1);
+  double binom = 1.0;  // C(k, m)
+  for (int m = 0; m <= k; ++m) {
+    s.c[k + m + 1] = c * binom * (((k - m) % 2) ? -1.0 : 1.0) / (k + m + 1);
+    binom = binom * (k - m) / (m + 1);
+  }
+  return s;
+}
+
+// v on [0, 1/2]; v(x) = 1 - v(1 - x) gives the rest (Lemma, Sec. 2.1).
+static double vhalf64(double x, const VSpec& vs) {
+  switch (vs.kind) {
+    case FFST_V_QUADRATIC:
+      return 2.0 * x * x;
+    case FFST_V_POLY: {
+      double acc = vs.c[vs.deg];
+      for (int n = vs.deg - 1; n >= 0; --n) acc = acc * x + vs.c[n];
+      return acc;
+    }
+    case FFST_V_CINF: {
+      if (x <= 0.0) return 0.0;
+      const double s0 = std::exp(-(1.0 / (x * x) + 1.0 / ((2.0 - x) * (2.0 - x))));
+      const double s1 = std::exp(-(1.0 / ((1.0 + x) * (1.0 + x)) + 1.0 / ((1.0 - x) * (1.0 - x))));
+      return s0 / (s0 + s1);
+    }
+    default: {
+      const double y2 = x * x;
+      return y2 * y2 * (35.0 + x * (-84.0 + x * (70.0 - 20.0 * x)));
+    }
+  }
+}
+
+static double v64(double x, const VSpec& vs) {
   if (x <= 0.0) return 0.0;
   if (x >= 1.0) return 1.0;
-  auto p = [](double y) {
-    const double y2 = y * y;
-    return y2 * y2 * (35.0 + y * (-84.0 + y * (70.0 - 20.0 * y)));
-  };
-  return x <= 0.5 ? p(x) : 1.0 - p(1.0 - x);
+  return x <= 0.5 ? vhalf64(x, vs) : 1.0 - vhalf64(1.0 - x, vs);
 }
 
 // psi1_hat in the closed form of Sec. 3.4 (equal to eq. (Psi1) of Sec. 2.1).
-static double psi1_64(double w) {
+static double psi1_64(double w, const VSpec& vs) {
   w = std::fabs(w);
   if (w <= 0.5) return 0.0;
-  if (w < 1.0) return std::sin(0.5 * kPi * v64(2.0 * w - 1.0));
+  if (w < 1.0) return std::sin(0.5 * kPi * v64(2.0 * w - 1.0, vs));
   if (w <= 2.0) return 1.0;
-  if (w < 4.0) return std::cos(0.5 * kPi * v64(0.5 * w - 1.0));
+  if (w < 4.0) return std::cos(0.5 * kPi * v64(0.5 * w - 1.0, vs));
   return 0.0;
 }
 
 // varphi of Sec. 2.4.
-static double varphi64(double w) {
+static double varphi64(double w, const VSpec& vs) {
   w = std::fabs(w);
   if (w <= 0.5) return 1.0;
-  if (w < 1.0) return std::cos(0.5 * kPi * v64(2.0 * w - 1.0));
+  if (w < 1.0) return std::cos(0.5 * kPi * v64(2.0 * w - 1.0, vs));
   return 0.0;
 }
 
 // 1 - varphi(w)^2, written as a sine square so it keeps full precision
 // where varphi is close to 1.
-static double varphi_sig64(double w) {
+static double varphi_sig64(double w, const VSpec& vs) {
   w = std::fabs(w);
   if (w <= 0.5) return 0.0;
   if (w < 1.0) {
-    const double s = std::sin(0.5 * kPi * v64(2.0 * w - 1.0));
+    const double s = std::sin(0.5 * kPi * v64(2.0 * w - 1.0, vs));
     return s * s;
   }
   return 1.0;
@@ -383,14 +426,24 @@ static cudaError_t upload(float2** dst, const std::vector<float2>& v) {
 using namespace ffst;
 
 extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* out) {
-  return ffst_plan_variant(rows, cols, scales, FFST_VARIANT_CLASSIC, out);
+  return ffst_plan_ex(rows, cols, scales, FFST_VARIANT_CLASSIC, FFST_V_MEYER, 0, FFST_MAXSCALE_MAX, out);
 }
 
-extern "C" ffst_status ffst_plan_variant(int rows, int cols, int scales, int variant, ffst_plan_t* out) {
+extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant, int vfun, int vorder, int max_scale,
+                                    ffst_plan_t* out) {
   if (!out) return fail(FFST_ERR_INVALID_ARG, "ffst_plan: out is NULL");
   *out = nullptr;
   if (variant != FFST_VARIANT_CLASSIC && variant != FFST_VARIANT_SMOOTH)
-    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_variant: variant must be FFST_VARIANT_CLASSIC or FFST_VARIANT_SMOOTH");
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_ex: variant must be FFST_VARIANT_CLASSIC or FFST_VARIANT_SMOOTH");
+  if (vfun < FFST_V_MEYER || vfun > FFST_V_CINF)
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_ex: vfun must be one of FFST_V_MEYER .. FFST_V_CINF");
+  if (vfun == FFST_V_POLY && (vorder < 1 || vorder > 7))
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_ex: FFST_V_POLY needs an order in 1..7");
+  if (max_scale != FFST_MAXSCALE_MAX && max_scale != FFST_MAXSCALE_MIN)
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_ex: max_scale must be FFST_MAXSCALE_MAX or FFST_MAXSCALE_MIN");
+  VSpec vs;
+  if (vfun == FFST_V_POLY) vs = v_poly_spec(vorder);
+  vs.kind = vfun;
   if (rows < 8 || cols < 8 || rows > 4096 || cols > 4096 || rows % 2 || cols % 2 || !supported_line(rows) ||
       !supported_line(cols / 2))
     return fail(FFST_ERR_UNSUPPORTED_SIZE,
@@ -436,8 +489,9 @@ extern "C" ffst_status ffst_plan_variant(int rows, int cols, int scales, int var
   }
   if ((int)p->planes.size() != p->eta) return fail(FFST_ERR_INVALID_ARG, "ffst_plan: internal plane count mismatch");
 
-  // FP64 window tables (Sec. 3.5.1 grid: xi = a * X / floor(L/2), X = 2^{2 j0 - 1})
-  const double X = std::ldexp(1.0, 2 * j0 - 1);
+  // FP64 window tables (Sec. 3.5.1 grid: xi = a * X / floor(L/2), X = 2^{2 j0 - 1},
+  // or X = 2^{2 j0 - 2} for max_scale = FFST_MAXSCALE_MIN)
+  const double X = std::ldexp(1.0, 2 * j0 - (max_scale == FFST_MAXSCALE_MAX ? 1 : 2));
   const double dc = X / p->hn, dr = X / p->hm;
   const int ncol = p->hn + 1, nrow = p->hm + 1;
   // layout: psi1 col [j0][ncol] | psi1 row [j0][nrow] | phi col | phi row |
@@ -455,20 +509,20 @@ extern "C" ffst_status ffst_plan_variant(int rows, int cols, int scales, int var
   for (int j = 0; j < j0; ++j) {
     const double a = std::ldexp(1.0, -2 * j);  // a_j = 4^-j
     for (int q = 0; q < ncol; ++q) {
-      psi1_col[(size_t)j * ncol + q] = (float)psi1_64(a * q * dc);
-      sig_col[(size_t)j * ncol + q] = (float)varphi_sig64(a * q * dc);
-      const double f = varphi64(0.25 * a * q * dc);
+      psi1_col[(size_t)j * ncol + q] = (float)psi1_64(a * q * dc, vs);
+      sig_col[(size_t)j * ncol + q] = (float)varphi_sig64(a * q * dc, vs);
+      const double f = varphi64(0.25 * a * q * dc, vs);
       alp_col[(size_t)j * ncol + q] = (float)(f * f);
     }
     for (int q = 0; q < nrow; ++q) {
-      psi1_row[(size_t)j * nrow + q] = (float)psi1_64(a * q * dr);
-      sig_row[(size_t)j * nrow + q] = (float)varphi_sig64(a * q * dr);
-      const double f = varphi64(0.25 * a * q * dr);
+      psi1_row[(size_t)j * nrow + q] = (float)psi1_64(a * q * dr, vs);
+      sig_row[(size_t)j * nrow + q] = (float)varphi_sig64(a * q * dr, vs);
+      const double f = varphi64(0.25 * a * q * dr, vs);
       alp_row[(size_t)j * nrow + q] = (float)(f * f);
     }
   }
-  for (int q = 0; q < ncol; ++q) phi_col[q] = (float)varphi64(q * dc);
-  for (int q = 0; q < nrow; ++q) phi_row[q] = (float)varphi64(q * dr);
+  for (int q = 0; q < ncol; ++q) phi_col[q] = (float)varphi64(q * dc, vs);
+  for (int q = 0; q < nrow; ++q) phi_row[q] = (float)varphi64(q * dr, vs);
 
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_tables, tab.size() * sizeof(float))) != cudaSuccess) return cuda_fail(e, "ffst_plan tables");
@@ -483,6 +537,9 @@ extern "C" ffst_status ffst_plan_variant(int rows, int cols, int scales, int var
   p->win.phi_col = p->win.psi1_row + (size_t)j0 * nrow;
   p->win.phi_row = p->win.phi_col + ncol;
   p->win.smooth = variant == FFST_VARIANT_SMOOTH;
+  p->win.vkind = vfun;
+  p->win.vdeg = vfun == FFST_V_POLY ? vs.deg : 0;
+  for (int n = 0; n < 16; ++n) p->win.vc[n] = (float)vs.c[n];
   p->win.sig_col = p->win.phi_row + nrow;
   p->win.sig_row = p->win.sig_col + (size_t)j0 * ncol;
   p->win.alp_col = p->win.sig_row + (size_t)j0 * nrow;

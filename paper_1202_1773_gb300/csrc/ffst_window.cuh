@@ -29,10 +29,27 @@ __device__ __forceinline__ float vpoly(float x) {
   return x2 * x2 * fmaf(x, fmaf(x, fmaf(x, -20.0f, 70.0f), -84.0f), 35.0f);
 }
 
-__device__ __forceinline__ float psi2_hat(float u) {
+// v(x) for x in [0, 1/2] in the plan's variant; v(1 - x) = 1 - v(x) covers
+// the other half in every variant.
+__device__ __forceinline__ float vhalf(const WinParams& w, float x) {
+  if (w.vkind == FFST_V_MEYER) return vpoly(x);
+  if (w.vkind == FFST_V_QUADRATIC) return 2.0f * x * x;
+  if (w.vkind == FFST_V_POLY) {
+    float acc = w.vc[w.vdeg];
+    for (int n = w.vdeg - 1; n >= 0; --n) acc = fmaf(acc, x, w.vc[n]);
+    return acc;
+  }
+  // FFST_V_CINF: s(x-1) / (s(x-1) + s(x)), s(y) = exp(-(1/(1+y)^2 + 1/(1-y)^2))
+  if (x <= 0.0f) return 0.0f;
+  const float s0 = expf(-(1.0f / (x * x) + 1.0f / ((2.0f - x) * (2.0f - x))));
+  const float s1 = expf(-(1.0f / ((1.0f + x) * (1.0f + x)) + 1.0f / ((1.0f - x) * (1.0f - x))));
+  return s0 / (s0 + s1);
+}
+
+__device__ __forceinline__ float psi2_hat(const WinParams& w, float u) {
   const float y = fabsf(u);
   if (y >= 1.0f) return 0.0f;
-  const float vv = (y < 0.5f) ? 1.0f - vpoly(y) : vpoly(1.0f - y);
+  const float vv = (y < 0.5f) ? 1.0f - vhalf(w, y) : vhalf(w, 1.0f - y);
   return sqrtf(vv);
 }
 
@@ -92,7 +109,7 @@ __device__ __forceinline__ float win_raw(const WinParams& w, int kappa, int j, i
   if (w.smooth) p1 = smooth_radial(w, j, a1, a2);  // both cones (Sec. 3.4 eq. smoothPsi)
   if (p1 == 0.0f) return 0.0f;
   const float u = __int2float_rn(num) / __int2float_rn(den);
-  return p1 * psi2_hat(u);
+  return p1 * psi2_hat(w, u);
 }
 
 // Spectrum with the Sec. 3.8.1 fix at half-spectrum position (pr, pc):

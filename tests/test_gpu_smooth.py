@@ -1,4 +1,6 @@
-"""Smooth-shearlet plans (ffst_plan_variant, Sec. 3.4) against the FP64 oracle.
+"""Construction options of ffst_plan_ex against the FP64 oracle: smooth
+shearlets (Sec. 3.4), variants of v (Sec. 2.1, Sec. 3.4 remark
+construction_v) and the grid extent maxScale (Sec. 3.5.1, Sec. 3.5.3).
 
 Same bars as the classic construction: spectra 1e-6 absolute, coefficient
 stack and reconstruction 1e-5 relative L2, Parseval frame on the GPU.
@@ -76,10 +78,42 @@ def test_smooth_stats_and_low_precision(ffst):
     p.close()
 
 
-def test_variant_code_checked(ffst):
+def test_option_codes_checked(ffst):
     from paper_1202_1773_gb300 import _lib
     import ctypes
 
     out = ctypes.c_void_p()
-    assert _lib.lib().ffst_plan_variant(64, 64, 0, 7, ctypes.byref(out)) == _lib.FFST_ERR_INVALID_ARG
-    assert out.value is None
+    for args in ((7, 0, 0, 0), (0, 9, 0, 0), (0, 2, 0, 0), (0, 2, 8, 0), (0, 0, 0, 3)):
+        assert _lib.lib().ffst_plan_ex(64, 64, 0, *args, ctypes.byref(out)) == _lib.FFST_ERR_INVALID_ARG
+        assert out.value is None
+    with pytest.raises(ValueError):
+        ffst.Plan(64, 64, vfun="cubic")
+    with pytest.raises(ValueError):
+        ffst.Plan(64, 64, max_scale="mid")
+
+
+OPTIONS = [
+    dict(vfun="quadratic"), dict(vfun=("poly", 1)), dict(vfun=("poly", 5)), dict(vfun="cinf"),
+    dict(max_scale="min"), dict(smooth=True, vfun="cinf", max_scale="min"),
+]
+ORACLE_KW = lambda kw: dict(smooth=kw.get("smooth", False), vfun=kw.get("vfun", "meyer"),
+                            max_scale=kw.get("max_scale", "max"))
+
+
+@pytest.mark.parametrize("kw", OPTIONS, ids=lambda kw: "-".join(f"{k}={v}" for k, v in kw.items()))
+@pytest.mark.parametrize("rows,cols,scales", [(64, 64, 3), (128, 256, 4)])
+def test_plan_options_match_oracle(ffst, kw, rows, cols, scales):
+    from oracle import ffst_oracle as o
+    from paper_1202_1773_gb300 import inputs
+
+    p = ffst.Plan(rows, cols, scales, **kw)
+    psi = p.spectra().cpu().numpy().astype(np.float64)
+    assert np.abs(psi - o.spectra(rows, cols, scales, **ORACLE_KW(kw))).max() <= 2e-6
+    f = inputs.scaled_cartoon(rows, cols, seed=33)
+    x = torch.from_numpy(f).cuda()
+    c = p.forward(x)
+    ref = o.forward(f.astype(np.float64), scales, **ORACLE_KW(kw))
+    assert np.linalg.norm(c.cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
+    r = p.inverse(c)
+    assert float(torch.linalg.norm(r - x) / torch.linalg.norm(x)) <= 1e-5
+    p.close()
