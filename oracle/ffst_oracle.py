@@ -463,3 +463,64 @@ def shrink(c: np.ndarray, tau, mode: str) -> np.ndarray:
     if mode == "hard":
         return np.where(np.abs(c) > t, c, 0.0)
     raise ValueError(f"unknown shrinkage mode {mode!r}")
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.8.2: complex (one-sided) shearlets
+# ---------------------------------------------------------------------------
+
+
+def half_plane(rows: int, cols: int, scales: int, i: int) -> np.ndarray:
+    """Selector h_i(omega) of the one-sided shearlet of plane i (FFT order).
+
+    Sec. 3.8.2 builds complex shearlets by keeping one side of each spectrum;
+    the paper does not say which side or what happens on the grid's
+    self-paired lines.  The reading used here: on C^h and the seam lines the
+    side omega_1 > 0, on C^v the side omega_2 > 0; on the Nyquist column
+    (omega_1 = -N/2) the side omega_2 > 0 and on the Nyquist row
+    (omega_2 = -M/2) the side omega_1 > 0, so that of every pair
+    {omega, -omega} exactly one point is kept (h + h(-.) = 1); the
+    self-conjugate points (omega = -omega on the grid) get 1/2; the low-pass
+    stays two-sided (h = 1/2 everywhere, so its complex coefficient is the
+    real one).
+    """
+    kappa, _, _ = plane_table(scales)[i]
+    if kappa == "lowpass":
+        return np.full((rows, cols), 0.5)
+    o1, o2, _, _ = grid(rows, cols, scales)
+    ch, cv, cx = cones(rows, cols, o1, o2)
+    ny_c = (cols % 2 == 0) & (o1 == -(cols // 2))
+    ny_r = (rows % 2 == 0) & (o2 == -(rows // 2))
+    s_h = np.where(ny_c, np.sign(np.where(ny_r, 0, o2)), np.sign(o1))
+    s_v = np.where(ny_r, np.sign(np.where(ny_c, 0, o1)), np.sign(o2))
+    s = np.where(ch | cx, s_h, np.where(cv, s_v, 0))
+    return 0.5 * (1.0 + s)
+
+
+def forward_onesided(f: np.ndarray, scales: int | None = None, **opts) -> np.ndarray:
+    """Complex coefficients z_i = sqrt(2) ifft2(psi_hat_i h_i fft2(f)), i >= 1, and
+    z_0 = ifft2(psi_hat_0 fft2(f)) (Sec. 3.8.2), shape (eta, M, N), complex.
+
+    With h_i + h_i(-.) = 1, Re z_i = c_i / sqrt(2) for i >= 1 and z_0 = c_0
+    for a real image (the frame property of the real transform carries over).
+    """
+    f = np.asarray(f, dtype=np.float64)
+    M, N = f.shape
+    if scales is None:
+        scales = default_scales(M, N)
+    F = np.fft.fft2(f)
+    out = []
+    for i in range(num_planes(scales)):
+        psi = spectrum(M, N, scales, i, **opts)
+        w = np.sqrt(2.0) * half_plane(M, N, scales, i) if i else 1.0
+        out.append(np.fft.ifft2(psi * w * F))
+    return np.stack(out)
+
+
+def inverse_onesided(z: np.ndarray, scales: int | None = None, **opts) -> np.ndarray:
+    """Image from one-sided coefficients: the real transform's inverse of
+    c_0 = Re z_0, c_i = sqrt(2) Re z_i (Sec. 3.8.2 with Sec. 3.3)."""
+    z = np.asarray(z)
+    c = np.sqrt(2.0) * np.real(z)
+    c[0] = np.real(z[0])
+    return inverse(c, scales, **opts)
