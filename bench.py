@@ -452,6 +452,16 @@ def run_forms(plan, pool, stack, rec, plain_value, args, dev):
                          "vs_plain": cps / (ms / 1e3) / plain_value, "threshold": "1.5 d(i) per plane, low-pass kept",
                          "kept_fraction": kept, "accuracy": {"mean_abs_rel_vs_stack_max": dmax}}
 
+    # one-sided complex shearlets (Sec. 3.8.2): planar complex stack, both parts and the inverse
+    zst = torch.empty((eta, 2, ROWS, COLS), device=dev)
+    ms = _time_steps(lambda q: (plan.forward_complex(pool[q % len(pool)], out=zst), plan.inverse_complex(zst, out=rec)),
+                     steps, dev)
+    plan.forward_complex(x0, out=zst)
+    err = float(torch.linalg.norm(plan.inverse_complex(zst) - x0)) / xnorm
+    out["complex"] = {"value": cps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "vs_plain": cps / (ms / 1e3) / plain_value,
+                      "stack_bytes": 2 * cps * 4, "accuracy": {"reconstruction_rel_l2": err}}
+    del zst
+
     # smooth shearlets (Sec. 3.4): a plan of the same size, same round trip
     sp = ffst.Plan(ROWS, COLS, SCALES, device=dev, smooth=True)
     ms = _time_steps(lambda q: (sp.forward(pool[q % len(pool)], out=stack), sp.inverse(stack, out=rec)), steps, dev)

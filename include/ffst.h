@@ -167,6 +167,22 @@ ffst_status ffst_forward_stats(ffst_plan_t plan, const float* img, void* coeffs,
                                int shrink, const float* thresh, float* mean_abs, void* stream);
 
 /*
+ * Complex shearlet coefficients from one-sided spectra (Sec. 3.8.2).  For a
+ * real image, z_i = sqrt(2) ifft2(psi_hat_i h_i fft2(img)) for i >= 1 and
+ * z_0 = the (real) low-pass coefficient, where h_i keeps one side of every
+ * pair {omega, -omega}: omega_1 > 0 on C^h and the seam lines, omega_2 > 0
+ * on C^v, the other axis deciding on the Nyquist column and row, 1/2 on the
+ * self-conjugate grid points.  Re z_i = c_i / sqrt(2) (c of ffst_forward),
+ * Im z_i = d_i / sqrt(2) with d_i the real transform for the multiplier
+ * -i sign(omega) psi_hat_i; |z_i| and arg z_i are the amplitude and phase.
+ *   coeffs  device float [eta][2][rows][cols], planar: Re z_i then Im z_i.
+ * ffst_forward_complex runs the real pipeline twice (both parts); FP32 only.
+ * ffst_inverse_complex reconstructs the image from the real parts.
+ */
+ffst_status ffst_forward_complex(ffst_plan_t plan, const float* img, float* coeffs, void* stream);
+ffst_status ffst_inverse_complex(ffst_plan_t plan, const float* coeffs, float* img, void* stream);
+
+/*
  * Inverse transform, Sec. 3.3 eq. (inverseShearletTransform), normalised by
  * sum_i psi_hat_i^2 (which the Parseval frame of Sec. 3.2 makes 1).
  *   coeffs:      device [eta][rows][cols] of the storage type, read only.

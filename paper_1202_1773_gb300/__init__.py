@@ -47,6 +47,8 @@ from ._lib import (  # noqa: F401
     ffst_forward,
     ffst_forward_noalloc,
     ffst_forward_stats,
+    ffst_forward_complex,
+    ffst_inverse_complex,
     ffst_inverse,
     ffst_plan,
     ffst_plan_info,
@@ -201,6 +203,33 @@ class Plan:
         if storage != FFST_STORE_F32:
             return out, mean_abs, plane_scale
         return out, mean_abs
+
+    def forward_complex(self, img, out=None):
+        """One-sided (complex) shearlet coefficients of Sec. 3.8.2 as a planar
+        float32 tensor [eta, 2, rows, cols] (real parts, imaginary parts);
+        ``torch.complex(z[:, 0], z[:, 1])`` gives a complex64 copy."""
+        torch = _torch()
+        self._check_img(img)
+        shape = (self.num_planes, 2, self.rows, self.cols)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=self.device)
+        if out.device != self.device or out.dtype != torch.float32 or tuple(out.shape) != shape \
+                or not out.is_contiguous():
+            raise ValueError(f"expected a contiguous float32 tensor of shape {shape} on {self.device}")
+        ffst_forward_complex(self.handle, img, out, self._stream())
+        return out
+
+    def inverse_complex(self, z, out=None):
+        """Image from a planar complex stack of forward_complex."""
+        torch = _torch()
+        shape = (self.num_planes, 2, self.rows, self.cols)
+        if z.device != self.device or z.dtype != torch.float32 or tuple(z.shape) != shape or not z.is_contiguous():
+            raise ValueError(f"expected a contiguous float32 tensor of shape {shape} on {self.device}")
+        if out is None:
+            out = torch.empty((self.rows, self.cols), dtype=torch.float32, device=self.device)
+        self._check_img(out)
+        ffst_inverse_complex(self.handle, z, out, self._stream())
+        return out
 
     def _synth(self, fn, coeffs, plane_scale, out):
         torch = _torch()

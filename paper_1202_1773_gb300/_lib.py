@@ -40,6 +40,8 @@ SIGNATURES = [
     ("ffst_adjoint", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
     ("ffst_forward_noalloc", _I, [_I, _I, _I, _VP, _VP, _VP]),
     ("ffst_forward_stats", _I, [_VP, _VP, _VP, _I, _VP, _I, _VP, _VP, _VP]),
+    ("ffst_forward_complex", _I, [_VP, _VP, _VP, _VP]),
+    ("ffst_inverse_complex", _I, [_VP, _VP, _VP, _VP]),
     ("ffst_plan_autotune", _I, [_VP, _I, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("ffst_plan_group_mb", _I, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("ffst_plan_set_schedule", _I, [_VP, _I]),
@@ -167,6 +169,14 @@ def ffst_forward(plan: int, img, coeffs, storage: int = FFST_STORE_F32, plane_sc
 def ffst_forward_stats(plan: int, img, coeffs, storage: int, plane_scale, shrink: int, thresh, mean_abs, stream: int):
     _check("ffst_forward_stats", lib().ffst_forward_stats(plan, _ptr(img), _ptr(coeffs), int(storage), _ptr(plane_scale),
                                                           int(shrink), _ptr(thresh), _ptr(mean_abs), stream))
+
+
+def ffst_forward_complex(plan: int, img, coeffs, stream: int):
+    _check("ffst_forward_complex", lib().ffst_forward_complex(plan, _ptr(img), _ptr(coeffs), stream))
+
+
+def ffst_inverse_complex(plan: int, coeffs, img, stream: int):
+    _check("ffst_inverse_complex", lib().ffst_inverse_complex(plan, _ptr(coeffs), _ptr(img), stream))
 
 
 def ffst_inverse(plan: int, coeffs, storage: int, plane_scale, img, stream=None):

@@ -68,7 +68,16 @@ static bool use_sched(const ffst_plan_s* p) { return p->sched.on && p->sched_mod
 
 static Group all_planes(const ffst_plan_s* p) { return Group{0, p->eta, 0, 0, p->total_items}; }
 
-static FwdColsArgs fwd_cols_args(const ffst_plan_s* p, const Group& g, float2* H, float* partials) {
+// Fused per-plane statistics and shrinkage of a forward (ffst_forward_stats).
+struct StatsOpts {
+  int shrink = 0;               // 0 none, 1 soft, 2 hard
+  const float* thresh = nullptr;
+  bool stats = false;           // accumulate sum |c| per (plane, row block)
+  int cplx_part = -1;           // one-sided complex stack (Sec. 3.8.2): 0 real parts, 1 imaginary parts
+};
+
+static FwdColsArgs fwd_cols_args(const ffst_plan_s* p, const Group& g, float2* H, float* partials,
+                                 const StatsOpts* so = nullptr) {
   FwdColsArgs a;
   a.F = p->d_F;
   a.Hc = p->Hc;
@@ -81,15 +90,10 @@ static FwdColsArgs fwd_cols_args(const ffst_plan_s* p, const Group& g, float2* H
   a.partials = partials ? partials + g.item0 : nullptr;
   a.gain = 1.0f / (kR2CGain * (float)p->M * (float)p->N);
   a.tmaps = p->d_tmaps;
+  a.odd = (so && so->cplx_part == 1) ? 1 : 0;
   return a;
 }
 
-// Fused per-plane statistics and shrinkage of a forward (ffst_forward_stats).
-struct StatsOpts {
-  int shrink = 0;               // 0 none, 1 soft, 2 hard
-  const float* thresh = nullptr;
-  bool stats = false;           // accumulate sum |c| per (plane, row block)
-};
 
 static C2RArgs plane_c2r_args(const ffst_plan_s* p, const Group& g, const float2* H, void* coeffs, int storage,
                               const float* plane_scale, const StatsOpts* so = nullptr) {
@@ -113,17 +117,28 @@ static C2RArgs plane_c2r_args(const ffst_plan_s* p, const Group& g, const float2
   a.thresh = so ? so->thresh : nullptr;
   a.abs_partials = (so && so->stats) ? p->d_abs_partials : nullptr;
   a.rbx = p->row_blocks;
+  a.cplx = 0;
+  if (so && so->cplx_part >= 0) {  // planar complex stack [eta][2][M][N]: this part of each plane
+    a.cplx = 1;
+    a.dst = static_cast<char*>(coeffs) + ((long long)g.p0 * 2 + so->cplx_part) * plane * sizeof(float);
+    a.dst_plane_stride = 2 * plane;
+  }
   return a;
 }
 
 static R2CArgs plane_r2c_args(const ffst_plan_s* p, const Group& g, const void* coeffs, int storage,
-                              const float* plane_scale, float2* H) {
+                              const float* plane_scale, float2* H, bool cplx = false) {
   const long long plane = (long long)p->M * p->N;
   R2CArgs a;
   a.src = static_cast<const char*>(coeffs) + (long long)g.p0 * plane * (storage == FFST_STORE_F32 ? 4 : 2);
   a.src_plane_stride = plane;
   a.st = storage;
   a.plane_scale = plane_scale;
+  a.cplx = cplx ? 1 : 0;
+  if (cplx) {  // real parts of the planar complex stack [eta][2][M][N]
+    a.src = static_cast<const char*>(coeffs) + (long long)g.p0 * 2 * plane * sizeof(float);
+    a.src_plane_stride = 2 * plane;
+  }
   a.plane0 = g.p0;
   a.M = p->M;
   a.dst = H;
@@ -188,13 +203,13 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
   if (use_sched(p)) {
     const Group all = all_planes(p);
     e = timed(p, kTimeFwdSched, (double)p->eta * plane * esz, s, [&] {
-      return launch_fwd_sched(p, fwd_cols_args(p, all, nullptr, partials),
+      return launch_fwd_sched(p, fwd_cols_args(p, all, nullptr, partials, so),
                               plane_c2r_args(p, all, nullptr, coeffs, storage, nullptr, so), target,
                               partials ? plane_scale : nullptr, s);
     });
   } else if (use_fused(p)) {
     e = timed(p, kTimeFwdCols, 0.0, s, [&] {
-      return launch_fwd_cols(p->M, fwd_cols_args(p, p->groups[0], hbuf(p, 0), partials), p->groups[0].nitems, s);
+      return launch_fwd_cols(p->M, fwd_cols_args(p, p->groups[0], hbuf(p, 0), partials, so), p->groups[0].nitems, s);
     });
     if (e == cudaSuccess) e = scales(0);
     for (size_t g = 1; g < G && e == cudaSuccess; ++g) {
@@ -202,7 +217,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
       const Group& rg = p->groups[g - 1];
       const double by = (double)(rg.p1 - rg.p0) * plane * esz;
       e = timed(p, kTimeFwdFused, by, s, [&] {
-        return launch_fwd_fused(p->M, fwd_cols_args(p, cg, hbuf(p, g), partials), cg.nitems,
+        return launch_fwd_fused(p->M, fwd_cols_args(p, cg, hbuf(p, g), partials, so), cg.nitems,
                                 plane_c2r_args(p, rg, hbuf(p, g - 1), coeffs, storage, plane_scale, so), rg.p1 - rg.p0,
                                 s);
       });
@@ -220,7 +235,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
       const Group& gr = p->groups[g];
       // group g's buffer is hbuf(g) as in the fused schedule (the TMA maps point there)
       e = timed(p, kTimeFwdCols, 0.0, s, [&] {
-        return launch_fwd_cols(p->M, fwd_cols_args(p, gr, hbuf(p, g), partials), gr.nitems, s);
+        return launch_fwd_cols(p->M, fwd_cols_args(p, gr, hbuf(p, g), partials, so), gr.nitems, s);
       });
       if (e == cudaSuccess) e = scales(g);
       if (e == cudaSuccess)
@@ -235,7 +250,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
 }
 
 static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, const float* plane_scale, float* img,
-                             cudaStream_t s, bool normalise) {
+                             cudaStream_t s, bool normalise, bool cplx = false) {
   const long long plane = (long long)p->M * p->N;
   const int esz = storage == FFST_STORE_F32 ? 4 : 2;
   const int Lr = p->N / 2;
@@ -246,14 +261,14 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
   if (use_sched(p)) {
     const Group all = all_planes(p);
     e = timed(p, kTimeInvSched, (double)p->eta * plane * esz, s, [&] {
-      return launch_inv_sched(p, plane_r2c_args(p, all, coeffs, storage, plane_scale, nullptr),
+      return launch_inv_sched(p, plane_r2c_args(p, all, coeffs, storage, plane_scale, nullptr, cplx),
                               inv_cols_args(p, all, nullptr), s);
     });
   } else if (use_fused(p)) {
     {
       const Group& rg = p->groups_inv[0];
       e = timed(p, kTimeInvRows, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
-        return launch_rows_r2c(Lr, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, 0)), rg.p1 - rg.p0,
+        return launch_rows_r2c(Lr, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, 0), cplx), rg.p1 - rg.p0,
                                s);
       });
     }
@@ -261,7 +276,7 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
       const Group& rg = p->groups_inv[g];
       const Group& cg = p->groups_inv[g - 1];
       e = timed(p, kTimeInvFused, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
-        return launch_inv_fused(p->M, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, g)), rg.p1 - rg.p0,
+        return launch_inv_fused(p->M, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, g), cplx), rg.p1 - rg.p0,
                                 inv_cols_args(p, cg, hbuf(p, g - 1)), npanels, s);
       });
     }
@@ -273,7 +288,7 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
     for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
       const Group& gr = p->groups_inv[g];
       e = timed(p, kTimeInvRows, (double)(gr.p1 - gr.p0) * plane * esz, s, [&] {
-        return launch_rows_r2c(Lr, plane_r2c_args(p, gr, coeffs, storage, plane_scale, hbuf(p, g)), gr.p1 - gr.p0,
+        return launch_rows_r2c(Lr, plane_r2c_args(p, gr, coeffs, storage, plane_scale, hbuf(p, g), cplx), gr.p1 - gr.p0,
                                s);
       });
       if (e == cudaSuccess)
@@ -296,6 +311,7 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
   oa.dst = img;
   oa.st = FFST_STORE_F32;
   oa.scale = 1.0f / (kR2CGain * (float)plane);
+  oa.cplx = 0;
   oa.tw = p->d_tw_rows;
   oa.rtw = p->d_rtw;
   e = timed(p, kTimeOutRows, 4.0 * plane, s, [&] { return launch_rows_c2r(Lr, oa, 1, s); });
@@ -341,6 +357,22 @@ extern "C" ffst_status ffst_forward_stats(ffst_plan_t plan, const float* img, vo
   const cudaError_t e = timed(plan, kTimeOther, 0.0, s, [&] { return launch_mean_abs(plan, mean_abs, s); });
   if (e != cudaSuccess) return cuda_fail(e, "ffst_forward_stats mean |c|");
   return FFST_OK;
+}
+
+extern "C" ffst_status ffst_forward_complex(ffst_plan_t plan, const float* img, float* coeffs, void* stream) {
+  if (!plan || !img || !coeffs) return fail(FFST_ERR_INVALID_ARG, "ffst_forward_complex: NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StatsOpts re, im;
+  re.cplx_part = 0;
+  im.cplx_part = 1;
+  ffst_status st = analysis(plan, img, coeffs, FFST_STORE_F32, nullptr, s, &re);
+  if (st == FFST_OK) st = analysis(plan, img, coeffs, FFST_STORE_F32, nullptr, s, &im);
+  return st;
+}
+
+extern "C" ffst_status ffst_inverse_complex(ffst_plan_t plan, const float* coeffs, float* img, void* stream) {
+  if (!plan || !coeffs || !img) return fail(FFST_ERR_INVALID_ARG, "ffst_inverse_complex: NULL argument");
+  return synthesis(plan, coeffs, FFST_STORE_F32, nullptr, img, static_cast<cudaStream_t>(stream), true, true);
 }
 
 extern "C" ffst_status ffst_inverse(ffst_plan_t plan, const void* coeffs, int storage, const float* plane_scale,

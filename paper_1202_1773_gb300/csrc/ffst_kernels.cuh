@@ -98,6 +98,7 @@ struct R2CArgs {
   long long src_plane_stride;
   int st;                    // storage code of src
   const float* plane_scale;  // per plane s_i (low-precision storage) or null
+  int cplx;                  // input is Re z of one-sided coefficients: c_i = sqrt(2) Re z_i, i >= 1
   int plane0;                // plane index of by == 0 (for descriptors/scales)
   int M;                     // rows
   float2* dst;               // grouped: base of the group's intermediate
@@ -122,6 +123,10 @@ __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, 
   if (!act) {
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = make_float2(0.f, 0.f);
+  } else if (a.cplx) {  // FP32 real parts of a complex stack, c_i = sqrt(2) Re z_i (i >= 1)
+    const float cs = plane == 0 ? 1.0f : 1.41421356237309505f;
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = cscale(load_pair(src, rbase + 2 * T * m, FFST_STORE_F32), cs);
   } else if (a.st == FFST_STORE_F32) {
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = load_pair(src, rbase + 2 * T * m, FFST_STORE_F32);
@@ -177,11 +182,13 @@ struct C2RArgs {
   const float* thresh;       // per-plane threshold on |c| (shrink != 0)
   float* abs_partials;       // per (plane, row block): sum |c| before shrinkage, or null
   int rbx;                   // row blocks per plane (stride of abs_partials)
+  int cplx;                  // complex planar output (Sec. 3.8.2): factor 1/sqrt(2) on planes i >= 1
 };
 
 // Factor s_i of plane a.plane0 + by for low-precision storage (1 otherwise),
 // read from the caller's per-plane scales.
 __device__ __forceinline__ float c2r_plane_factor(const C2RArgs& a, int by) {
+  if (a.cplx) return (a.plane0 + by) == 0 ? 1.0f : 0.70710678118654752f;  // z_i = (c_i + i d_i) / sqrt(2)
   return (a.st != FFST_STORE_F32 && a.plane_scale) ? __ldg(&a.plane_scale[a.plane0 + by]) : 1.0f;
 }
 
@@ -338,6 +345,7 @@ struct FwdColsArgs {
   float* partials;          // per item sum |G| (low-precision storage), or null
   float gain;               // G = gain * psi_hat * F (folds the 1/(M N) of the inverse DFT)
   const CUtensorMap* tmaps; // per plane: tensor map of its slot (TMA panel stores), or null
+  int odd;                  // one-sided shearlets, imaginary part: G = -i sign(omega) G (Sec. 3.8.2)
 };
 
 // Forward column items per block.  A block walks kFwdItems consecutive items
@@ -379,6 +387,7 @@ __device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int blk, flo
       const int row = mod_l<L>(rg.x + t);
       f = a.F[(long long)row * a.Hc + c];
       psi = win_at(a.w, d, row, c);
+      if (a.odd) psi *= (float)half_sign(a.w, d.kappa, row, c);
     }
   };
   float2 f0;
@@ -392,15 +401,18 @@ __device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int blk, flo
     const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
     float mag = 0.0f;
     if (t < rg.y) {
-      const float2 g = cscale(f0, psi0 * a.gain);
+      float2 g = cscale(f0, psi0 * a.gain);
+      if (a.odd) g = make_float2(g.y, -g.x);  // -i g (the sign is in psi0)
       buf[spad<E>(mod_l<L>(rg.x + t))] = g;
       if (a.partials) mag += sqrtf(g.x * g.x + g.y * g.y);
     }
     for (int q = t + T; q < rg.y; q += T) {
       const int row = mod_l<L>(rg.x + q);
-      const float psi = win_at(a.w, d, row, c);
+      float psi = win_at(a.w, d, row, c);
+      if (a.odd) psi *= (float)half_sign(a.w, d.kappa, row, c);
       float2 g = make_float2(0.f, 0.f);
       if (psi != 0.0f) g = cscale(a.F[(long long)row * a.Hc + c], psi * a.gain);
+      if (a.odd) g = make_float2(g.y, -g.x);
       buf[spad<E>(row)] = g;
       if (a.partials) mag += sqrtf(g.x * g.x + g.y * g.y);
     }

@@ -294,6 +294,7 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
     ca.partials = nullptr;
     ca.gain = 1.0f / (kR2CGain * (float)plane);
     ca.tmaps = nullptr;
+    ca.odd = 0;
     e = launch_fwd_cols(rows, ca, (p1 - p0) * su.ipp, s);
     if (e != cudaSuccess) break;
     C2RArgs ra;

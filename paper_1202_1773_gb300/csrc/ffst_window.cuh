@@ -128,4 +128,22 @@ __device__ __forceinline__ float win_at(const WinParams& w, const PlaneDesc& d, 
   return sqrtf(0.5f * (a * a + b * b));
 }
 
+// Side of the one-sided (complex) shearlets of Sec. 3.8.2 at half-spectrum
+// position (pr, pc): +1 kept, -1 dropped, 0 on the self-conjugate grid
+// points and for the low-pass (two-sided).  On C^h and the seam lines the
+// side omega_1 > 0, on C^v omega_2 > 0; on the Nyquist column the sign of
+// omega_2 decides and on the Nyquist row the sign of omega_1, so that of
+// every pair {omega, -omega} exactly one point is kept.
+__device__ __forceinline__ int half_sign(const WinParams& w, int kappa, int pr, int pc) {
+  if (kappa == kLowpass) return 0;
+  const int o2 = (2 * pr < w.M) ? pr : pr - w.M;
+  const int o1 = (2 * pc < w.N) ? pc : pc - w.N;
+  const bool ny_r = (w.M % 2 == 0) && (2 * pr == w.M);
+  const bool ny_c = (w.N % 2 == 0) && (2 * pc == w.N);
+  auto sgn = [](int x) { return (x > 0) - (x < 0); };
+  const bool use_h = abs(o2) * w.hn <= abs(o1) * w.hm;  // C^h, seam lines (and the origin)
+  if (use_h) return ny_c ? (ny_r ? 0 : sgn(o2)) : sgn(o1);
+  return ny_r ? (ny_c ? 0 : sgn(o1)) : sgn(o2);
+}
+
 }  // namespace ffst

@@ -61,6 +61,8 @@ def test_null_arguments_rejected_on_host(lib):
     assert lib.ffst_plane_index(None, 0, None, None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_forward(None, None, None, 0, None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_forward_stats(None, None, None, 0, None, 0, None, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_forward_complex(None, None, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_inverse_complex(None, None, None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_inverse(None, None, 0, None, None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_adjoint(None, None, 0, None, None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_spectra(None, None, None) == _lib.FFST_ERR_INVALID_ARG
