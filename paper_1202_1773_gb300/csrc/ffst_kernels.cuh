@@ -85,6 +85,16 @@ struct ColCfg {
   static_assert(P * T == kThreads, "column teams must fill the block");
 };
 
+// v[m] for a runtime m (a chain of selects, no local memory).
+template <int E>
+__device__ __forceinline__ float2 pick(const float2 (&v)[E], int m) {
+  float2 r = v[0];
+#pragma unroll
+  for (int k = 1; k < E; ++k)
+    if (m == k) r = v[k];
+  return r;
+}
+
 template <int M>
 __device__ __forceinline__ bool in_range(int row, int2 rg) {
   return mod_l<M>(row - rg.x) < rg.y;
@@ -527,7 +537,50 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
     const PlaneDesc d = a.planes[p];
     const bool act = c >= d.c0 && c < d.c0 + d.W;
     const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
-    // first support row of this thread: accumulator value and window, ahead of the FFT
+    if (tma) {
+      // Rows t + T m of the support interval stay with the thread that holds
+      // them after the FFT: it accumulates them from its registers, so the
+      // shared buffers are free as soon as the FFT ends and the next plane's
+      // panel load overlaps the accumulation.  A row always belongs to the
+      // same thread, so the sums stay in plane order without a barrier.
+      unsigned mask = 0;
+#pragma unroll
+      for (int m = 0; m < E; ++m)
+        if (in_range<L>(t + T * m, rg)) mask |= 1u << m;
+      const int m0 = mask ? __ffs(mask) - 1 : 0;
+      const int row0 = t + T * m0;
+      float2 s0 = make_float2(0.f, 0.f);
+      float psi0 = 0.0f;
+      if (mask) {  // first row's accumulator and window, ahead of the FFT
+        s0 = __ldcg(&a.S[(long long)row0 * a.Hc + c]);
+        psi0 = win_at(a.w, d, row0, c);
+      }
+      if (!__syncthreads_and(mbar_wait(&mbar, phase, a.err))) return;
+      phase ^= 1;
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = act ? smem[(t + T * m) * P + cl] : make_float2(0.f, 0.f);
+      __syncthreads();  // panel read before the FFT reuses the buffers
+      line_fft<L, E, false, kSyncBlock>(v, buf, t, a.tw);  // ends with a barrier after its last buffer read
+      const int pn = next_plane(p + 1);
+      if (pn < a.p1) issue_panel(pn);
+      if (mask) {
+        const float2 x = pick(v, m0);
+        a.S[(long long)row0 * a.Hc + c] = make_float2(fmaf(psi0, x.x, s0.x), fmaf(psi0, x.y, s0.y));
+        for (unsigned rest = mask & (mask - 1); rest; rest &= rest - 1) {
+          const int m = __ffs(rest) - 1;
+          const int row = t + T * m;
+          const float psi = win_at(a.w, d, row, c);
+          const float2 y = pick(v, m);
+          float2* sp = a.S + (long long)row * a.Hc + c;
+          const float2 old = __ldcg(sp);
+          *sp = make_float2(fmaf(psi, y.x, old.x), fmaf(psi, y.y, old.y));
+        }
+      }
+      p = pn;
+      continue;
+    }
+    // plain loads: the support rows go through the shared buffers to
+    // consecutive threads while the next plane's column loads fly
     const bool first = t < rg.y;
     const int row0 = mod_l<L>(rg.x + t);
     float2 s0 = make_float2(0.f, 0.f);
@@ -536,13 +589,6 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
       s0 = __ldcg(&a.S[(long long)row0 * a.Hc + c]);
       psi0 = win_at(a.w, d, row0, c);
     }
-    if (tma) {
-      if (!__syncthreads_and(mbar_wait(&mbar, phase, a.err))) return;
-      phase ^= 1;
-#pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = act ? smem[(t + T * m) * P + cl] : make_float2(0.f, 0.f);
-      __syncthreads();  // panel read before the FFT reuses the buffers
-    }
     line_fft<L, E, false, kSyncBlock>(v, buf, t, a.tw);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -550,7 +596,7 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
       if (in_range<L>(row, rg)) buf[spad<E>(row)] = v[m];
     }
     const int pn = next_plane(p + 1);
-    if (!tma && pn < a.p1) load_cols(pn, v);
+    if (pn < a.p1) load_cols(pn, v);
     __syncthreads();
     if (first) {
       const float2 x = buf[spad<E>(row0)];
@@ -565,7 +611,6 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
       *sp = make_float2(fmaf(psi, x.x, old.x), fmaf(psi, x.y, old.y));
     }
     __syncthreads();  // buf reads and S writes done before the next plane
-    if (tma && pn < a.p1) issue_panel(pn);
     p = pn;
   }
 }
