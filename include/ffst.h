@@ -264,6 +264,25 @@ ffst_status ffst_plan_group_mb(ffst_plan_t plan, double* fwd_mb, double* inv_mb)
 ffst_status ffst_plan_set_schedule(ffst_plan_t plan, int mode);
 ffst_status ffst_plan_get_schedule(ffst_plan_t plan, int* mode);
 
+/*
+ * Plane chunks of the inverse's column pass (implementation choice, no
+ * counterpart in the paper).  The sum over planes of the inverse and the
+ * adjoint (Sec. 3.3) runs as nsplit partial sums: chunk k takes the planes
+ * [eta k / nsplit, eta (k + 1) / nsplit), each added in plane order into its
+ * own [rows][cols/2+1] accumulator, and the final column pass adds the
+ * partial sums in chunk order.  More chunks give more parallel column
+ * blocks where the panels alone do not fill the GPU (small images); the
+ * rounding order, and so the last bits of the result, depend on nsplit but
+ * not on the schedule mode or the group budgets.  ffst_plan picks the
+ * chunks for about four column blocks per SM (1 at 2048x2048 and above, up
+ * to 16 for small images; the environment variable FFST_INV_SPLIT at plan
+ * creation overrides); nsplit = 0 restores that choice.  Partial
+ * accumulators are allocated on demand (nsplit x rows x (cols/2+1) x 8
+ * bytes).  FFST_ERR_INVALID_ARG for nsplit outside 0..16.
+ */
+ffst_status ffst_plan_set_inverse_split(ffst_plan_t plan, int nsplit);
+ffst_status ffst_plan_get_inverse_split(ffst_plan_t plan, int* nsplit);
+
 /* Shape of the persistent schedule (zeros until it is built): resident
  * blocks per launch, tasks in the forward and inverse queues, ring size in
  * MB.  Any output pointer may be NULL. */

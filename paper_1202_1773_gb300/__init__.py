@@ -40,9 +40,11 @@ from ._lib import (  # noqa: F401
     ffst_plan_autotune,
     ffst_plan_batched,
     ffst_plan_check,
+    ffst_plan_get_inverse_split,
     ffst_plan_get_schedule,
     ffst_plan_group_mb,
     ffst_plan_schedule_info,
+    ffst_plan_set_inverse_split,
     ffst_plan_set_schedule,
     ffst_forward,
     ffst_forward_noalloc,
@@ -269,6 +271,15 @@ class Plan:
     @schedule.setter
     def schedule(self, mode: int):
         ffst_plan_set_schedule(self.handle, mode)
+
+    @property
+    def inverse_split(self) -> int:
+        """Plane chunks of the inverse column pass (ffst_plan_set_inverse_split)."""
+        return ffst_plan_get_inverse_split(self.handle)
+
+    @inverse_split.setter
+    def inverse_split(self, nsplit: int):
+        ffst_plan_set_inverse_split(self.handle, nsplit)
 
     def schedule_info(self) -> dict:
         """Resident blocks, forward/inverse task counts and ring size of the persistent schedule."""

@@ -46,6 +46,8 @@ SIGNATURES = [
     ("ffst_plan_group_mb", _I, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("ffst_plan_set_schedule", _I, [_VP, _I]),
     ("ffst_plan_get_schedule", _I, [_VP, ctypes.POINTER(_I)]),
+    ("ffst_plan_set_inverse_split", _I, [_VP, _I]),
+    ("ffst_plan_get_inverse_split", _I, [_VP, ctypes.POINTER(_I)]),
     ("ffst_plan_check", _I, [_VP, _VP]),
     ("ffst_plan_schedule_info", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                                      ctypes.POINTER(ctypes.c_double)]),
@@ -220,6 +222,16 @@ def ffst_plan_get_schedule(plan: int) -> int:
 def ffst_plan_check(plan: int, stream: int = 0) -> int:
     """Status of the bounded device-side waits since the last check (0 = FFST_OK); raises nothing."""
     return int(lib().ffst_plan_check(plan, stream))
+
+
+def ffst_plan_set_inverse_split(plan: int, nsplit: int):
+    _check("ffst_plan_set_inverse_split", lib().ffst_plan_set_inverse_split(plan, int(nsplit)))
+
+
+def ffst_plan_get_inverse_split(plan: int) -> int:
+    n = _I()
+    _check("ffst_plan_get_inverse_split", lib().ffst_plan_get_inverse_split(plan, ctypes.byref(n)))
+    return n.value
 
 
 def ffst_plan_schedule_info(plan: int) -> dict:

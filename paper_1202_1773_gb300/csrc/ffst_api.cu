@@ -160,6 +160,12 @@ static InvColsArgs inv_cols_args(const ffst_plan_s* p, const Group& g, const flo
   a.p1 = g.p1;
   a.rng = p->d_rng;
   a.S = p->d_S;
+  a.sstride = (long long)p->M * p->Hc;
+  a.npanels = (p->Hc + cols_per_cta(p->M) - 1) / cols_per_cta(p->M);
+  a.eta = p->eta;
+  a.nsplit = p->inv_split;
+  a.k0 = g.p1 > g.p0 ? inv_part(p, g.p0) : 0;
+  a.nchunks = g.p1 > g.p0 ? inv_part(p, g.p1 - 1) - a.k0 + 1 : 0;
   a.w = p->win;
   a.tw = p->d_tw_cols;
   a.tmaps = p->d_tmaps_inv;
@@ -254,8 +260,8 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
   const long long plane = (long long)p->M * p->N;
   const int esz = storage == FFST_STORE_F32 ? 4 : 2;
   const int Lr = p->N / 2;
-  const int npanels = (p->Hc + cols_per_cta(p->M) - 1) / cols_per_cta(p->M);
-  cudaError_t e = cudaMemsetAsync(p->d_S, 0, sizeof(float2) * (size_t)p->M * p->Hc, s);
+  const long long spec = (long long)p->M * p->Hc;
+  cudaError_t e = cudaMemsetAsync(p->d_S, 0, sizeof(float2) * (size_t)(p->inv_split * spec), s);
   if (e != cudaSuccess) return cuda_fail(e, "inverse accumulator clear");
   const size_t G = p->groups_inv.size();
   if (use_sched(p)) {
@@ -277,12 +283,12 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
       const Group& cg = p->groups_inv[g - 1];
       e = timed(p, kTimeInvFused, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
         return launch_inv_fused(p->M, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, g), cplx), rg.p1 - rg.p0,
-                                inv_cols_args(p, cg, hbuf(p, g - 1)), npanels, s);
+                                inv_cols_args(p, cg, hbuf(p, g - 1)), s);
       });
     }
     if (e == cudaSuccess)
       e = timed(p, kTimeInvCols, 0.0, s, [&] {
-        return launch_inv_cols(p->M, inv_cols_args(p, p->groups_inv[G - 1], hbuf(p, G - 1)), npanels, s);
+        return launch_inv_cols(p->M, inv_cols_args(p, p->groups_inv[G - 1], hbuf(p, G - 1)), s);
       });
   } else {
     for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
@@ -293,12 +299,13 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
       });
       if (e == cudaSuccess)
         e = timed(p, kTimeInvCols, 0.0, s,
-                  [&] { return launch_inv_cols(p->M, inv_cols_args(p, gr, hbuf(p, g)), npanels, s); });
+                  [&] { return launch_inv_cols(p->M, inv_cols_args(p, gr, hbuf(p, g)), s); });
     }
   }
   if (e != cudaSuccess) return cuda_fail(e, "inverse plane passes");
   e = timed(p, kTimeOutCols, 0.0, s, [&] {
-    return launch_cols_fft(p->M, p->d_S, p->Hc, p->Hc, true, normalise ? p->d_invD : nullptr, p->d_tw_cols, s);
+    return launch_cols_fft(p->M, p->d_S, p->Hc, p->Hc, true, normalise ? p->d_invD : nullptr, p->d_tw_cols, s,
+                           p->inv_split, spec);
   });
   if (e != cudaSuccess) return cuda_fail(e, "inverse final column pass");
   C2RArgs oa;
@@ -399,6 +406,20 @@ extern "C" ffst_status ffst_plan_set_schedule(ffst_plan_t plan, int mode) {
     if (st != FFST_OK) return st;
   }
   plan->sched_mode = mode;
+  return FFST_OK;
+}
+
+extern "C" ffst_status ffst_plan_set_inverse_split(ffst_plan_t plan, int nsplit) {
+  if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_inverse_split: plan is NULL");
+  if (nsplit < 0 || nsplit > kMaxInvSplit)
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_inverse_split: nsplit must be in 0..16");
+  if (nsplit == 0) nsplit = plan->inv_split_default;
+  return plan_set_inv_split(plan, nsplit);
+}
+
+extern "C" ffst_status ffst_plan_get_inverse_split(ffst_plan_t plan, int* nsplit) {
+  if (!plan || !nsplit) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_get_inverse_split: NULL argument");
+  *nsplit = plan->inv_split;
   return FFST_OK;
 }
 

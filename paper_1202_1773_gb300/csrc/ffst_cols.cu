@@ -7,9 +7,9 @@ namespace ffst {
 template <int L, bool INV>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS)
     k_cols_fft(float2* __restrict__ buf, int width, int ld, const float* __restrict__ scale_tab,
-               const float2* __restrict__ tw) {
+               const float2* __restrict__ tw, int nsum, long long sstride) {
   extern __shared__ __align__(128) float2 smem[];
-  cols_fft_body<L, INV>(buf, width, ld, scale_tab, tw, blockIdx.x, smem);
+  cols_fft_body<L, INV>(buf, width, ld, scale_tab, tw, nsum, sstride, blockIdx.x, smem);
 }
 
 template <int L>
@@ -21,7 +21,10 @@ __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_fwd_cols(FwdColsA
 template <int L>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_inv_cols(InvColsArgs a) {
   extern __shared__ __align__(128) float2 smem[];
-  inv_cols_body<L>(a, blockIdx.x, smem);
+  int q0, q1;
+  float2* S;
+  const int panel = inv_chunk(a, blockIdx.x, &q0, &q1, &S);
+  inv_cols_body<L>(a, panel, q0, q1, S, smem);
 }
 
 int cols_per_cta(int L) {
@@ -48,15 +51,15 @@ int cols_per_cta(int L) {
 
 template <int L>
 static cudaError_t cols_fft_L(float2* buf, int width, int ld, bool inverse, const float* scale_tab,
-                              const float2* tw, cudaStream_t s) {
+                              const float2* tw, int nsum, long long sstride, cudaStream_t s) {
   const int grid = (width + ColCfg<L>::P - 1) / ColCfg<L>::P;
   cudaError_t e;
   if (inverse) {
     if ((e = set_smem(k_cols_fft<L, true>, ColCfg<L>::SMEM)) != cudaSuccess) return e;
-    k_cols_fft<L, true><<<grid, kThreads, ColCfg<L>::SMEM, s>>>(buf, width, ld, scale_tab, tw);
+    k_cols_fft<L, true><<<grid, kThreads, ColCfg<L>::SMEM, s>>>(buf, width, ld, scale_tab, tw, nsum, sstride);
   } else {
     if ((e = set_smem(k_cols_fft<L, false>, ColCfg<L>::SMEM)) != cudaSuccess) return e;
-    k_cols_fft<L, false><<<grid, kThreads, ColCfg<L>::SMEM, s>>>(buf, width, ld, scale_tab, tw);
+    k_cols_fft<L, false><<<grid, kThreads, ColCfg<L>::SMEM, s>>>(buf, width, ld, scale_tab, tw, nsum, sstride);
   }
   return cudaGetLastError();
 }
@@ -73,10 +76,12 @@ static cudaError_t fwd_cols_L(const FwdColsArgs& a, int nitems, cudaStream_t s) 
 }
 
 template <int L>
-static cudaError_t inv_cols_L(const InvColsArgs& a, int npanels, cudaStream_t s) {
+static cudaError_t inv_cols_L(const InvColsArgs& a, cudaStream_t s) {
+  const int nb = a.npanels * a.nchunks;
+  if (nb <= 0) return cudaSuccess;
   cudaError_t e = set_smem(k_inv_cols<L>, ColCfg<L>::SMEM);
   if (e != cudaSuccess) return e;
-  k_inv_cols<L><<<npanels, kThreads, ColCfg<L>::SMEM, s>>>(a);
+  k_inv_cols<L><<<nb, kThreads, ColCfg<L>::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -102,8 +107,8 @@ static cudaError_t inv_cols_L(const InvColsArgs& a, int npanels, cudaStream_t s)
   }
 
 cudaError_t launch_cols_fft(int L, float2* buf, int width, int ld, bool inverse, const float* scale_tab,
-                            const float2* tw, cudaStream_t s) {
-#define CALL_(LL) cols_fft_L<LL>(buf, width, ld, inverse, scale_tab, tw, s)
+                            const float2* tw, cudaStream_t s, int nsum, long long sstride) {
+#define CALL_(LL) cols_fft_L<LL>(buf, width, ld, inverse, scale_tab, tw, nsum, sstride, s)
   FFST_DISPATCH_COL(L, CALL_)
 #undef CALL_
 }
@@ -114,8 +119,8 @@ cudaError_t launch_fwd_cols(int L, const FwdColsArgs& a, int nitems, cudaStream_
 #undef CALL_
 }
 
-cudaError_t launch_inv_cols(int L, const InvColsArgs& a, int npanels, cudaStream_t s) {
-#define CALL_(LL) inv_cols_L<LL>(a, npanels, s)
+cudaError_t launch_inv_cols(int L, const InvColsArgs& a, cudaStream_t s) {
+#define CALL_(LL) inv_cols_L<LL>(a, s)
   FFST_DISPATCH_COL(L, CALL_)
 #undef CALL_
 }

@@ -30,8 +30,14 @@ template <int M>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_inv_fused(R2CArgs ra, int rbx, InvColsArgs ca, int nc) {
   extern __shared__ __align__(128) float2 smem[];
   int ci = 0, ri = 0;
-  if (split_cols_first(blockIdx.x, nc, &ci, &ri)) inv_cols_body<M>(ca, ci, smem);
-  else rows_r2c_body<M / 2>(ra, ri % rbx, ri / rbx, smem);
+  if (split_cols_first(blockIdx.x, nc, &ci, &ri)) {
+    int q0, q1;
+    float2* S;
+    const int panel = inv_chunk(ca, ci, &q0, &q1, &S);
+    inv_cols_body<M>(ca, panel, q0, q1, S, smem);
+  } else {
+    rows_r2c_body<M / 2>(ra, ri % rbx, ri / rbx, smem);
+  }
 }
 
 template <int M>
@@ -49,7 +55,8 @@ static cudaError_t fwd_fused_M(const FwdColsArgs& ca, int nitems, const C2RArgs&
 }
 
 template <int M>
-static cudaError_t inv_fused_M(const R2CArgs& ra, int nplanes, const InvColsArgs& ca, int nc, cudaStream_t s) {
+static cudaError_t inv_fused_M(const R2CArgs& ra, int nplanes, const InvColsArgs& ca, cudaStream_t s) {
+  const int nc = ca.npanels * ca.nchunks;
   const int rbx = (ra.M + RowCfg<M / 2>::TEAMS - 1) / RowCfg<M / 2>::TEAMS;
   const int nr = rbx * nplanes;
   if (nc + nr == 0) return cudaSuccess;
@@ -78,8 +85,8 @@ cudaError_t launch_fwd_fused(int M, const FwdColsArgs& ca, int nitems, const C2R
 #undef CALL_
 }
 
-cudaError_t launch_inv_fused(int M, const R2CArgs& ra, int nplanes, const InvColsArgs& ca, int nc, cudaStream_t s) {
-#define CALL_(MM) inv_fused_M<MM>(ra, nplanes, ca, nc, s)
+cudaError_t launch_inv_fused(int M, const R2CArgs& ra, int nplanes, const InvColsArgs& ca, cudaStream_t s) {
+#define CALL_(MM) inv_fused_M<MM>(ra, nplanes, ca, s)
   FFST_DISPATCH_FUSED(M, CALL_)
 #undef CALL_
 }

@@ -249,6 +249,7 @@ struct Sched {
   int4* d_pdep = nullptr;               // per plane: ring predecessors [x, y], their batches [z, w]
   int2* d_batch = nullptr;              // per inverse batch: planes [x, y)
   int* d_batch_tasks = nullptr;         // per inverse batch: column tasks
+  int* d_batch_part = nullptr;          // per inverse batch: partial accumulator
   int* d_ctl = nullptr;                 // per launch counters (zeroed before each launch)
   int ctl_ints = 0;
   int off_cols = 0, off_rows = 0, off_batch = 0, off_panel = 0;  // counter arrays inside d_ctl
@@ -271,7 +272,10 @@ struct ffst_plan_s {
   float2* d_tw_cols = nullptr;          // pass twiddles of the column lines (M, col_E)
   int2* d_rng = nullptr;                // per (plane, support column): cyclic row range (start, len)
   float2* d_F = nullptr;                // [M][Hc] image spectrum
-  float2* d_S = nullptr;                // [M][Hc] inverse accumulator
+  float2* d_S = nullptr;                // inv_split x [M][Hc] inverse partial accumulators
+  int inv_split = 1;                    // plane chunks per inverse group (partial accumulators)
+  int inv_split_cap = 0;                // partial accumulators allocated
+  int inv_split_default = 1;            // the plan's choice at creation
   float* d_invD = nullptr;              // [M][Hc] 1 / sum_i psi_i^2 (FP32 psi), inverse normalisation
   float2* d_H = nullptr;                // two group intermediates (double buffer), h_elems each
   long long h_elems = 0;
@@ -303,6 +307,13 @@ ffst_status cuda_fail(cudaError_t e, const char* what);
 // plan grouping and autotuning (ffst_plan.cu, ffst_autotune.cu)
 void default_group_mb(double* fwd_mb, double* inv_mb);
 ffst_status plan_regroup(ffst_plan_s* p, double fwd_mb, double inv_mb);
+// Plane chunks of the inverse column pass: chunk k of inv_split holds the
+// planes [eta k / inv_split, eta (k + 1) / inv_split) (the device's
+// inv_chunk boundaries) and is summed into partial accumulator k, whatever
+// the plane groups; inv_part gives a plane's k.
+constexpr int kMaxInvSplit = 16;
+int inv_part(const ffst_plan_s* p, int plane);
+ffst_status plan_set_inv_split(ffst_plan_s* p, int n);
 bool autotune_lookup(const ffst_plan_s* p, int storage, double* fwd_mb, double* inv_mb);
 
 // timing helpers

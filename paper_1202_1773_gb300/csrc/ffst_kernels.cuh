@@ -315,12 +315,15 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
 // column passes
 // ---------------------------------------------------------------------------
 
-// In-place column FFTs of columns [0, width) of buf (row stride ld).  When
-// `scale_tab` is given (same layout), each element is multiplied by it first.
+// In-place column FFTs of columns [0, width) of buf (row stride ld).  With
+// nsum > 1 the input is the sum of nsum arrays of that layout, sstride
+// elements apart (the inverse's partial accumulators), added in index order
+// and written to the first.  When `scale_tab` is given (same layout), each
+// element is multiplied by it next.
 template <int L, bool INV>
 __device__ __forceinline__ void cols_fft_body(float2* __restrict__ buf, int width, int ld,
                                               const float* __restrict__ scale_tab, const float2* __restrict__ tw,
-                                              int bx, float2* smem) {
+                                              int nsum, long long sstride, int bx, float2* smem) {
   constexpr int E = ColCfg<L>::E, T = ColCfg<L>::T, P = ColCfg<L>::P;
   const int t = threadIdx.x / P, cl = threadIdx.x % P;
   const int c = bx * P + cl;
@@ -330,6 +333,14 @@ __device__ __forceinline__ void cols_fft_body(float2* __restrict__ buf, int widt
   float2 v[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = act ? col[m * step] : make_float2(0.f, 0.f);
+  for (int k = 1; k < nsum && act; ++k) {
+    const float2* part = col + k * sstride;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const float2 y = __ldcs(&part[m * step]);
+      v[m] = make_float2(v[m].x + y.x, v[m].y + y.y);
+    }
+  }
   if (scale_tab && act) {
     const float* sc = scale_tab + (long long)t * ld + c;
 #pragma unroll
@@ -472,28 +483,43 @@ struct InvColsArgs {
   const PlaneDesc* planes;
   int p0, p1;               // planes of the group
   const int2* rng;
-  float2* S;                // [M][Hc] accumulator (zeroed before the first group)
+  float2* S;                // nsplit partial accumulators [M][Hc] (zeroed before the first group)
+  long long sstride;        // elements between partial accumulators
+  int npanels;              // column panels
+  int eta, nsplit;          // plane chunk k: planes [eta k / nsplit, eta (k + 1) / nsplit)
+  int k0, nchunks;          // the chunks that meet [p0, p1)
   WinParams w;
   const float2* tw;
   const CUtensorMap* tmaps; // per plane: tensor map of its slot (TMA panel loads), or null
   int* err;                 // sticky error word (a TMA wait that ran out sets bit 2)
 };
 
+// Block bx of an inverse column launch (npanels x nchunks blocks): panel
+// bx % npanels over the group's planes in chunk k = k0 + bx / npanels,
+// summed into partial accumulator k.
+__device__ __forceinline__ int inv_chunk(const InvColsArgs& a, int bx, int* q0, int* q1, float2** S) {
+  const int j = bx / a.npanels, k = a.k0 + j;
+  *q0 = max(a.p0, (int)((long long)a.eta * k / a.nsplit));
+  *q1 = min(a.p1, (int)((long long)a.eta * (k + 1) / a.nsplit));
+  *S = a.S + k * a.sstride;
+  return bx - j * a.npanels;
+}
+
 // Inverse column pass (Sec. 3.3 eq. inverseShearletTransform): for every plane
-// of the group whose support meets this block's panel, column FFT of the
-// plane's row spectra, then S += psi_hat_i * (that) on the column's support
-// rows (one cyclic interval, walked by consecutive threads through the
-// team's shared buffer).  Each block owns its columns and visits planes in
+// of [p0, p1) whose support meets panel bx, column FFT of the plane's row
+// spectra, then S += psi_hat_i * (that) on the column's support rows (one
+// cyclic interval).  Each block owns its columns of S and visits planes in
 // index order, so the sums are deterministic.  S is read through L2: in the
 // persistent schedule successive plane batches of a panel may run on
 // different SMs.
 //
-// Software pipeline: the next plane's column loads are issued as soon as
-// the current spectrum is parked in shared memory, so they fly during the
-// accumulation; a thread's first accumulator element and its window value
-// are fetched before the FFT, while the plane's own loads are in flight.
+// Software pipeline: the next plane's panel (TMA) or column loads are issued
+// as soon as the current spectrum has left the shared buffers, so they fly
+// during the accumulation; a thread's first accumulator element and its
+// window value are fetched before the FFT.
 template <int L>
-__device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, float2* smem) {
+__device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, int p0, int p1, float2* S,
+                                              float2* smem) {
   constexpr int E = ColCfg<L>::E, T = ColCfg<L>::T, P = ColCfg<L>::P;
   __shared__ uint64_t mbar;  // TMA panel loads
   const int t = threadIdx.x / P, cl = threadIdx.x % P;
@@ -503,7 +529,7 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
   const bool tma = a.tmaps != nullptr;
   // next plane at or after p whose support meets the panel (uniform over the block)
   auto next_plane = [&](int p) {
-    for (; p < a.p1; ++p) {
+    for (; p < p1; ++p) {
       const int c0 = a.planes[p].c0, W = a.planes[p].W;
       if (W != 0 && c0 < cbase + P && c0 + W > cbase) break;
     }
@@ -527,13 +553,13 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
     __syncthreads();
   }
   unsigned phase = 0;
-  int p = next_plane(a.p0);
+  int p = next_plane(p0);
   float2 v[E];
-  if (p < a.p1) {
+  if (p < p1) {
     if (tma) issue_panel(p);
     else load_cols(p, v);
   }
-  while (p < a.p1) {
+  while (p < p1) {
     const PlaneDesc d = a.planes[p];
     const bool act = c >= d.c0 && c < d.c0 + d.W;
     const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
@@ -552,7 +578,7 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
       float2 s0 = make_float2(0.f, 0.f);
       float psi0 = 0.0f;
       if (mask) {  // first row's accumulator and window, ahead of the FFT
-        s0 = __ldcg(&a.S[(long long)row0 * a.Hc + c]);
+        s0 = __ldcg(&S[(long long)row0 * a.Hc + c]);
         psi0 = win_at(a.w, d, row0, c);
       }
       if (!__syncthreads_and(mbar_wait(&mbar, phase, a.err))) return;
@@ -562,16 +588,16 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
       __syncthreads();  // panel read before the FFT reuses the buffers
       line_fft<L, E, false, kSyncBlock>(v, buf, t, a.tw);  // ends with a barrier after its last buffer read
       const int pn = next_plane(p + 1);
-      if (pn < a.p1) issue_panel(pn);
+      if (pn < p1) issue_panel(pn);
       if (mask) {
         const float2 x = pick(v, m0);
-        a.S[(long long)row0 * a.Hc + c] = make_float2(fmaf(psi0, x.x, s0.x), fmaf(psi0, x.y, s0.y));
+        S[(long long)row0 * a.Hc + c] = make_float2(fmaf(psi0, x.x, s0.x), fmaf(psi0, x.y, s0.y));
         for (unsigned rest = mask & (mask - 1); rest; rest &= rest - 1) {
           const int m = __ffs(rest) - 1;
           const int row = t + T * m;
           const float psi = win_at(a.w, d, row, c);
           const float2 y = pick(v, m);
-          float2* sp = a.S + (long long)row * a.Hc + c;
+          float2* sp = S + (long long)row * a.Hc + c;
           const float2 old = __ldcg(sp);
           *sp = make_float2(fmaf(psi, y.x, old.x), fmaf(psi, y.y, old.y));
         }
@@ -586,7 +612,7 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
     float2 s0 = make_float2(0.f, 0.f);
     float psi0 = 0.0f;
     if (first) {
-      s0 = __ldcg(&a.S[(long long)row0 * a.Hc + c]);
+      s0 = __ldcg(&S[(long long)row0 * a.Hc + c]);
       psi0 = win_at(a.w, d, row0, c);
     }
     line_fft<L, E, false, kSyncBlock>(v, buf, t, a.tw);
@@ -596,17 +622,17 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, floa
       if (in_range<L>(row, rg)) buf[spad<E>(row)] = v[m];
     }
     const int pn = next_plane(p + 1);
-    if (pn < a.p1) load_cols(pn, v);
+    if (pn < p1) load_cols(pn, v);
     __syncthreads();
     if (first) {
       const float2 x = buf[spad<E>(row0)];
-      a.S[(long long)row0 * a.Hc + c] = make_float2(fmaf(psi0, x.x, s0.x), fmaf(psi0, x.y, s0.y));
+      S[(long long)row0 * a.Hc + c] = make_float2(fmaf(psi0, x.x, s0.x), fmaf(psi0, x.y, s0.y));
     }
     for (int q = t + T; q < rg.y; q += T) {
       const int row = mod_l<L>(rg.x + q);
       const float psi = win_at(a.w, d, row, c);
       const float2 x = buf[spad<E>(row)];
-      float2* sp = a.S + (long long)row * a.Hc + c;
+      float2* sp = S + (long long)row * a.Hc + c;
       const float2 old = __ldcg(sp);
       *sp = make_float2(fmaf(psi, x.x, old.x), fmaf(psi, x.y, old.y));
     }
@@ -631,9 +657,9 @@ __device__ __forceinline__ bool split_cols_first(int b, int nc, int* ci, int* ri
 cudaError_t launch_rows_r2c(int L, const R2CArgs& a, int nplanes, cudaStream_t s);
 cudaError_t launch_rows_c2r(int L, const C2RArgs& a, int nplanes, cudaStream_t s);
 cudaError_t launch_cols_fft(int L, float2* buf, int width, int ld, bool inverse, const float* scale_tab,
-                            const float2* tw, cudaStream_t s);
+                            const float2* tw, cudaStream_t s, int nsum = 1, long long sstride = 0);
 cudaError_t launch_fwd_cols(int L, const FwdColsArgs& a, int nitems, cudaStream_t s);
-cudaError_t launch_inv_cols(int L, const InvColsArgs& a, int npanels, cudaStream_t s);
+cudaError_t launch_inv_cols(int L, const InvColsArgs& a, cudaStream_t s);  // a.npanels x a.nchunks blocks
 // Fused launches exist for square images with 256 <= M <= 4096 (fused_supported);
 // other sizes return cudaErrorNotSupported and use the standalone kernels.
 bool fused_supported(int M, int N);
@@ -645,6 +671,6 @@ cudaError_t launch_fwd_sched(const ffst_plan_s* p, FwdColsArgs ca, C2RArgs ra, f
 cudaError_t launch_inv_sched(const ffst_plan_s* p, R2CArgs ra, InvColsArgs ca, cudaStream_t st);
 cudaError_t launch_fwd_fused(int M, const FwdColsArgs& ca, int nitems, const C2RArgs& ra, int nplanes,
                              cudaStream_t s);
-cudaError_t launch_inv_fused(int M, const R2CArgs& ra, int nplanes, const InvColsArgs& ca, int nc, cudaStream_t s);
+cudaError_t launch_inv_fused(int M, const R2CArgs& ra, int nplanes, const InvColsArgs& ca, cudaStream_t s);
 
 }  // namespace ffst

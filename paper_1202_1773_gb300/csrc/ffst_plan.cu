@@ -393,6 +393,42 @@ ffst_status plan_regroup(ffst_plan_s* p, double fwd_mb, double inv_mb) {
   return tma_build(p, off_f, off_i);
 }
 
+int inv_part(const ffst_plan_s* p, int plane) {
+  for (int k = 0; k < p->inv_split; ++k)
+    if (plane < (int)((long long)p->eta * (k + 1) / p->inv_split)) return k;
+  return p->inv_split - 1;
+}
+
+// Default plane chunks of the inverse column pass: enough column blocks
+// (panels x chunks) for about four resident blocks per SM, at most
+// kMaxInvSplit; FFST_INV_SPLIT overrides.  At 2048x2048 the 513 panels
+// already fill the GPU (one chunk); at 512x512 there are only 33.
+static int default_inv_split(const ffst_plan_s* p) {
+  if (const char* s = std::getenv("FFST_INV_SPLIT")) {
+    const int n = std::atoi(s);
+    if (n >= 1) return std::min(n, kMaxInvSplit);
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || sms < 1) sms = 1;
+  const int P = cols_per_cta(p->M);
+  const int npanels = (p->Hc + P - 1) / P;
+  return std::max(1, std::min(kMaxInvSplit, 4 * sms / npanels));
+}
+
+ffst_status plan_set_inv_split(ffst_plan_s* p, int n) {
+  if (n < 1 || n > kMaxInvSplit) return fail(FFST_ERR_INVALID_ARG, "inverse split must be in 1..16");
+  if (n > p->inv_split_cap) {
+    float2* d = nullptr;
+    const cudaError_t e = cudaMalloc(&d, (size_t)n * p->M * p->Hc * sizeof(float2));
+    if (e != cudaSuccess) return cuda_fail(e, "inverse partial accumulators");
+    cudaFree(p->d_S);
+    p->d_S = d;
+    p->inv_split_cap = n;
+  }
+  p->inv_split = n;
+  return p->sched.on ? sched_build(p, p->sched.ring_mb) : FFST_OK;
+}
+
 // Pass twiddle table of a line (L, E) (layout in ffst_fft.cuh), FP64 -> FP32.
 static std::vector<float2> pass_table(int L, int E) {
   std::vector<float2> t(L > 1 ? L : 1, make_float2(1.0f, 0.0f));
@@ -608,7 +644,11 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
     if ((e = cudaMalloc(&p->d_abs_partials, sizeof(float) * (size_t)p->eta * p->row_blocks)) != cudaSuccess)
       return cuda_fail(e, "statistics partials");
   }
-  if ((e = cudaMalloc(&p->d_S, spec * sizeof(float2))) != cudaSuccess) return cuda_fail(e, "workspace S");
+  {
+    p->inv_split_default = default_inv_split(p.get());
+    const ffst_status st = plan_set_inv_split(p.get(), p->inv_split_default);
+    if (st != FFST_OK) return st;
+  }
   if ((e = cudaMalloc(&p->d_invD, spec * sizeof(float))) != cudaSuccess) return cuda_fail(e, "normalisation");
   if ((e = launch_inv_norm(p.get(), 0)) != cudaSuccess) return cuda_fail(e, "ffst_plan normalisation");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "ffst_plan");

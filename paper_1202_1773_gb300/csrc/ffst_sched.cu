@@ -46,6 +46,7 @@ struct SchedArgs {
   const int4* pdep;
   const int2* batch;
   const int* batch_tasks;
+  const int* batch_part;  // per inverse batch: its partial accumulator
   int rbx;         // row tasks per plane
   float target;    // per-plane scale target of low-precision storage (0: FP32 stack)
   float* scale_out;  // per-plane scales written by the forward (low-precision storage)
@@ -201,10 +202,7 @@ __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS)
       }
       __syncthreads();
       if (!ok) return;
-      InvColsArgs cb = ca;
-      cb.p0 = pr.x;
-      cb.p1 = pr.y;
-      inv_cols_body<M>(cb, task.z, smem);
+      inv_cols_body<M>(ca, task.z, pr.x, pr.y, ca.S + s.batch_part[b] * ca.sstride, smem);
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();
@@ -281,6 +279,7 @@ static SchedArgs sched_args(const ffst_plan_s* p, bool fwd) {
   s.pdep = sc.d_pdep;
   s.batch = sc.d_batch;
   s.batch_tasks = sc.d_batch_tasks;
+  s.batch_part = sc.d_batch_part;
   s.rbx = sc.rbx;
   s.target = 0.0f;
   s.scale_out = nullptr;
@@ -355,6 +354,7 @@ void sched_free(ffst_plan_s* p) {
   cudaFree(sc.d_pdep);
   cudaFree(sc.d_batch);
   cudaFree(sc.d_batch_tasks);
+  cudaFree(sc.d_batch_part);
   cudaFree(sc.d_ctl);
   sc = Sched{};
 }
@@ -404,16 +404,19 @@ ffst_status sched_build(ffst_plan_s* p, double ring_mb) {
         pdep[i].y = q;
       }
   }
-  // inverse batches: consecutive planes with at most a third of the ring each
+  // inverse batches: consecutive planes with at most a third of the ring
+  // each, all summed into the same partial accumulator as in the grouped
+  // launches (so both schedules add the same terms in the same order)
   std::vector<int2> batch;
-  std::vector<int> batch_of(eta);
+  std::vector<int> batch_of(eta), batch_part;
   {
     long long acc = 0;
     int b0 = 0;
     for (int i = 0; i < eta; ++i) {
       const long long n = (long long)M * rp[i].ldw;
-      if (i > b0 && acc + n > ring / 3) {
+      if (i > b0 && (acc + n > ring / 3 || inv_part(p, i) != inv_part(p, b0))) {
         batch.push_back(make_int2(b0, i));
+        batch_part.push_back(inv_part(p, b0));
         b0 = i;
         acc = 0;
       }
@@ -421,6 +424,7 @@ ffst_status sched_build(ffst_plan_s* p, double ring_mb) {
       batch_of[i] = (int)batch.size();
     }
     batch.push_back(make_int2(b0, eta));
+    batch_part.push_back(inv_part(p, b0));
   }
   sc.nbatch = (int)batch.size();
   for (int i = 0; i < eta; ++i)
@@ -578,6 +582,7 @@ ffst_status sched_build(ffst_plan_s* p, double ring_mb) {
   if (e == cudaSuccess) e = upload(&sc.d_pdep, pdep);
   if (e == cudaSuccess) e = upload(&sc.d_batch, batch);
   if (e == cudaSuccess) e = upload(&sc.d_batch_tasks, batch_tasks);
+  if (e == cudaSuccess) e = upload(&sc.d_batch_part, batch_part);
   if (e == cudaSuccess) e = cudaMalloc(&sc.d_ctl, sizeof(int) * (size_t)sc.ctl_ints);
   if (e != cudaSuccess) {
     sched_free(p);

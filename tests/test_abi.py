@@ -71,6 +71,8 @@ def test_null_arguments_rejected_on_host(lib):
     assert lib.ffst_plan_get_schedule(None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_plan_check(None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_plan_schedule_info(None, None, None, None, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_plan_set_inverse_split(None, 1) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_plan_get_inverse_split(None, None) == _lib.FFST_ERR_INVALID_ARG
     lib.ffst_destroy(None)  # no-op
     with pytest.raises(_lib.FFSTError):
         _lib.ffst_plan(64, 48, 0)
