@@ -30,11 +30,15 @@
  *    host before anything is enqueued; FFST_ERR_CUDA reports a failed CUDA
  *    runtime call (launch or allocation), after which the outputs are
  *    unspecified.
- *  - Supported sizes: rows and cols even, 8 <= rows, cols <= 4096, rows a
- *    power of two or one of 240, 320, 384, 480, 640, 768 (factors 2, 3, 5),
- *    cols/2 a power of two or one of those (so 480x640 and 768x1024 work);
- *    scales in 1..8 (or <= 0 for the default j0 of Sec. 3.1).  Other sizes
- *    return FFST_ERR_UNSUPPORTED_SIZE.
+ *  - Supported sizes: 8 <= rows, cols <= 4096, odd and prime sizes included;
+ *    scales in 1..8 (or <= 0 for the default j0 of Sec. 3.1).  Columns of a
+ *    height that is a power of two or one of 240, 320, 384, 480, 640, 768,
+ *    and rows of a width that is twice one of those, run native FFT lines;
+ *    any other height or width (at most 2048) runs Bluestein lines (a DFT of
+ *    length n as a chirp convolution through power-of-two FFTs, several times
+ *    slower per line) and never the fused or persistent launches.  Other
+ *    sizes return FFST_ERR_UNSUPPORTED_SIZE.  ffst_forward_noalloc keeps its
+ *    own limits (powers of two).
  */
 #ifndef FFST_H
 #define FFST_H

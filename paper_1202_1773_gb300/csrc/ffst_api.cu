@@ -9,7 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 
-#include "ffst_kernels.cuh"
+#include "ffst_blue.cuh"
 
 namespace ffst {
 
@@ -75,6 +75,32 @@ struct StatsOpts {
   bool stats = false;           // accumulate sum |c| per (plane, row block)
   int cplx_part = -1;           // one-sided complex stack (Sec. 3.8.2): 0 real parts, 1 imaginary parts
 };
+
+// Line passes at the plan's sizes: native FFT lines, or generic (Bluestein)
+// lines for a dimension without them (ffst_blue.cuh).  Generic sizes never
+// take the fused or persistent launches (fused_supported).
+static cudaError_t rows_r2c(const ffst_plan_s* p, const R2CArgs& a, int nplanes, cudaStream_t s) {
+  return p->bl_rows.n ? launch_blue_rows_r2c(p->bl_rows, a, nplanes, s) : launch_rows_r2c(p->N / 2, a, nplanes, s);
+}
+
+static cudaError_t rows_c2r(const ffst_plan_s* p, const C2RArgs& a, int nplanes, cudaStream_t s) {
+  return p->bl_rows.n ? launch_blue_rows_c2r(p->bl_rows, a, nplanes, s) : launch_rows_c2r(p->N / 2, a, nplanes, s);
+}
+
+static cudaError_t cols_fft(const ffst_plan_s* p, float2* buf, bool inverse, const float* scale_tab, cudaStream_t s,
+                            int nsum = 1, long long sstride = 0) {
+  return p->bl_cols.n
+             ? launch_blue_cols_fft(p->bl_cols, buf, p->Hc, p->Hc, inverse, scale_tab, s, nsum, sstride)
+             : launch_cols_fft(p->M, buf, p->Hc, p->Hc, inverse, scale_tab, p->d_tw_cols, s, nsum, sstride);
+}
+
+static cudaError_t fwd_cols(const ffst_plan_s* p, const FwdColsArgs& a, int nitems, cudaStream_t s) {
+  return p->bl_cols.n ? launch_blue_fwd_cols(p->bl_cols, a, nitems, s) : launch_fwd_cols(p->M, a, nitems, s);
+}
+
+static cudaError_t inv_cols(const ffst_plan_s* p, const InvColsArgs& a, cudaStream_t s) {
+  return p->bl_cols.n ? launch_blue_inv_cols(p->bl_cols, a, s) : launch_inv_cols(p->M, a, s);
+}
 
 static FwdColsArgs fwd_cols_args(const ffst_plan_s* p, const Group& g, float2* H, float* partials,
                                  const StatsOpts* so = nullptr) {
@@ -161,7 +187,7 @@ static InvColsArgs inv_cols_args(const ffst_plan_s* p, const Group& g, const flo
   a.rng = p->d_rng;
   a.S = p->d_S;
   a.sstride = (long long)p->M * p->Hc;
-  a.npanels = (p->Hc + cols_per_cta(p->M) - 1) / cols_per_cta(p->M);
+  a.npanels = (p->Hc + p->P - 1) / p->P;
   a.eta = p->eta;
   a.nsplit = p->inv_split;
   a.k0 = g.p1 > g.p0 ? inv_part(p, g.p0) : 0;
@@ -177,7 +203,6 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
                             cudaStream_t s, const StatsOpts* so = nullptr) {
   const long long plane = (long long)p->M * p->N;
   const int esz = storage == FFST_STORE_F32 ? 4 : 2;
-  const int Lr = p->N / 2;
   cudaError_t e;
   // fft2 of the image: row R2C into F, then column FFT in place
   R2CArgs ia;
@@ -191,10 +216,10 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
   ia.ld = p->Hc;
   ia.tw = p->d_tw_rows;
   ia.rtw = p->d_rtw;
-  e = timed(p, kTimeImgRows, 4.0 * plane, s, [&] { return launch_rows_r2c(Lr, ia, 1, s); });
+  e = timed(p, kTimeImgRows, 4.0 * plane, s, [&] { return rows_r2c(p, ia, 1, s); });
   if (e != cudaSuccess) return cuda_fail(e, "forward image row pass");
   e = timed(p, kTimeImgCols, 0.0, s,
-            [&] { return launch_cols_fft(p->M, p->d_F, p->Hc, p->Hc, false, nullptr, p->d_tw_cols, s); });
+            [&] { return cols_fft(p, p->d_F, false, nullptr, s); });
   if (e != cudaSuccess) return cuda_fail(e, "forward image column pass");
 
   float* partials = storage == FFST_STORE_F32 ? nullptr : p->d_partials;
@@ -215,7 +240,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
     });
   } else if (use_fused(p)) {
     e = timed(p, kTimeFwdCols, 0.0, s, [&] {
-      return launch_fwd_cols(p->M, fwd_cols_args(p, p->groups[0], hbuf(p, 0), partials, so), p->groups[0].nitems, s);
+      return fwd_cols(p, fwd_cols_args(p, p->groups[0], hbuf(p, 0), partials, so), p->groups[0].nitems, s);
     });
     if (e == cudaSuccess) e = scales(0);
     for (size_t g = 1; g < G && e == cudaSuccess; ++g) {
@@ -232,7 +257,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
     if (e == cudaSuccess) {
       const Group& rg = p->groups[G - 1];
       e = timed(p, kTimeFwdRows, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
-        return launch_rows_c2r(Lr, plane_c2r_args(p, rg, hbuf(p, G - 1), coeffs, storage, plane_scale, so),
+        return rows_c2r(p, plane_c2r_args(p, rg, hbuf(p, G - 1), coeffs, storage, plane_scale, so),
                                rg.p1 - rg.p0, s);
       });
     }
@@ -241,12 +266,12 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
       const Group& gr = p->groups[g];
       // group g's buffer is hbuf(g) as in the fused schedule (the TMA maps point there)
       e = timed(p, kTimeFwdCols, 0.0, s, [&] {
-        return launch_fwd_cols(p->M, fwd_cols_args(p, gr, hbuf(p, g), partials, so), gr.nitems, s);
+        return fwd_cols(p, fwd_cols_args(p, gr, hbuf(p, g), partials, so), gr.nitems, s);
       });
       if (e == cudaSuccess) e = scales(g);
       if (e == cudaSuccess)
         e = timed(p, kTimeFwdRows, (double)(gr.p1 - gr.p0) * plane * esz, s, [&] {
-          return launch_rows_c2r(Lr, plane_c2r_args(p, gr, hbuf(p, g), coeffs, storage, plane_scale, so), gr.p1 - gr.p0,
+          return rows_c2r(p, plane_c2r_args(p, gr, hbuf(p, g), coeffs, storage, plane_scale, so), gr.p1 - gr.p0,
                                  s);
         });
     }
@@ -259,7 +284,6 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
                              cudaStream_t s, bool normalise, bool cplx = false) {
   const long long plane = (long long)p->M * p->N;
   const int esz = storage == FFST_STORE_F32 ? 4 : 2;
-  const int Lr = p->N / 2;
   const long long spec = (long long)p->M * p->Hc;
   cudaError_t e = cudaMemsetAsync(p->d_S, 0, sizeof(float2) * (size_t)(p->inv_split * spec), s);
   if (e != cudaSuccess) return cuda_fail(e, "inverse accumulator clear");
@@ -274,7 +298,7 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
     {
       const Group& rg = p->groups_inv[0];
       e = timed(p, kTimeInvRows, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
-        return launch_rows_r2c(Lr, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, 0), cplx), rg.p1 - rg.p0,
+        return rows_r2c(p, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, 0), cplx), rg.p1 - rg.p0,
                                s);
       });
     }
@@ -288,24 +312,23 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
     }
     if (e == cudaSuccess)
       e = timed(p, kTimeInvCols, 0.0, s, [&] {
-        return launch_inv_cols(p->M, inv_cols_args(p, p->groups_inv[G - 1], hbuf(p, G - 1)), s);
+        return inv_cols(p, inv_cols_args(p, p->groups_inv[G - 1], hbuf(p, G - 1)), s);
       });
   } else {
     for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
       const Group& gr = p->groups_inv[g];
       e = timed(p, kTimeInvRows, (double)(gr.p1 - gr.p0) * plane * esz, s, [&] {
-        return launch_rows_r2c(Lr, plane_r2c_args(p, gr, coeffs, storage, plane_scale, hbuf(p, g), cplx), gr.p1 - gr.p0,
+        return rows_r2c(p, plane_r2c_args(p, gr, coeffs, storage, plane_scale, hbuf(p, g), cplx), gr.p1 - gr.p0,
                                s);
       });
       if (e == cudaSuccess)
         e = timed(p, kTimeInvCols, 0.0, s,
-                  [&] { return launch_inv_cols(p->M, inv_cols_args(p, gr, hbuf(p, g)), s); });
+                  [&] { return inv_cols(p, inv_cols_args(p, gr, hbuf(p, g)), s); });
     }
   }
   if (e != cudaSuccess) return cuda_fail(e, "inverse plane passes");
   e = timed(p, kTimeOutCols, 0.0, s, [&] {
-    return launch_cols_fft(p->M, p->d_S, p->Hc, p->Hc, true, normalise ? p->d_invD : nullptr, p->d_tw_cols, s,
-                           p->inv_split, spec);
+    return cols_fft(p, p->d_S, true, normalise ? p->d_invD : nullptr, s, p->inv_split, spec);
   });
   if (e != cudaSuccess) return cuda_fail(e, "inverse final column pass");
   C2RArgs oa;
@@ -321,7 +344,7 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
   oa.cplx = 0;
   oa.tw = p->d_tw_rows;
   oa.rtw = p->d_rtw;
-  e = timed(p, kTimeOutRows, 4.0 * plane, s, [&] { return launch_rows_c2r(Lr, oa, 1, s); });
+  e = timed(p, kTimeOutRows, 4.0 * plane, s, [&] { return rows_c2r(p, oa, 1, s); });
   if (e != cudaSuccess) return cuda_fail(e, "inverse final row pass");
   return FFST_OK;
 }

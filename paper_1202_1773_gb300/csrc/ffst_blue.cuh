@@ -1,0 +1,99 @@
+// Lines of any length n (odd, prime, or even without a native FFT kernel):
+// Bluestein's chirp-z form of the DFT (L. Bluestein, "A linear filtering
+// approach to the computation of the discrete Fourier transform", 1970),
+// run on the power-of-two register FFTs of ffst_fft.cuh.
+//
+// With the chirp w_j = exp(-i pi j^2 / n), jk = (j^2 + k^2 - (k - j)^2) / 2
+// turns the DFT into a convolution:
+//   X[k] = w_k sum_j (x_j w_j) conj(w_{k-j}),   0 <= j, k < n,
+// evaluated as a cyclic convolution of length L2 (a power of two >= 2n - 1,
+// so the filter's wrapped taps do not overlap) through two FFTs of length L2
+// and a pointwise product with the filter's precomputed spectrum.  The
+// inverse DFT (e^{+2 pi i jk/n}) is conj(DFT(conj x)).
+//
+// The generic passes below carry the same argument structs and the same
+// contracts as the native ones of ffst_kernels.cuh (the Sec. 3.1 forward and
+// Sec. 3.3 inverse of the shearlet transform on half spectra), with one
+// line per team of T = L2/E threads:
+//   rows: two real rows per complex line (z = x_a + i x_b), consecutive
+//         threads on consecutive elements;
+//   columns: P columns per block, interleaved across the warps.
+#pragma once
+
+#include "ffst_kernels.cuh"
+
+namespace ffst {
+
+// BlueLine (the tables of one dimension) is declared in ffst_internal.cuh.
+constexpr int kBlueMinL2 = 16;
+constexpr int kBlueMaxL2 = 4096;  // lines up to n = 2048
+
+// Columns (lines) per block of the generic column (row) passes.
+int blue_lines_per_block(int L2);
+
+// Host tables of a line of length n (FP64, rounded to FP32).
+void blue_tables(int n, int* L2, std::vector<float2>* chirp, std::vector<float2>* bhat);
+
+cudaError_t launch_blue_rows_r2c(const BlueLine& b, const R2CArgs& a, int nplanes, cudaStream_t s);
+cudaError_t launch_blue_rows_c2r(const BlueLine& b, const C2RArgs& a, int nplanes, cudaStream_t s);
+cudaError_t launch_blue_cols_fft(const BlueLine& b, float2* buf, int width, int ld, bool inverse,
+                                 const float* scale_tab, cudaStream_t s, int nsum = 1, long long sstride = 0);
+cudaError_t launch_blue_fwd_cols(const BlueLine& b, const FwdColsArgs& a, int nitems, cudaStream_t s);
+cudaError_t launch_blue_inv_cols(const BlueLine& b, const InvColsArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// device side (included by ffst_blue_rows.cu and ffst_blue_cols.cu)
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+// One element of a stack (any storage code), streaming like load_pair.
+__device__ __forceinline__ float load_one(const void* p, long long i, int st) {
+  if (st == FFST_STORE_F32) return __ldcs(static_cast<const float*>(p) + i);
+  if (st == FFST_STORE_F16) return __half2float(__ldcs(static_cast<const __half*>(p) + i));
+  return __bfloat162float(__ldcs(static_cast<const __nv_bfloat16*>(p) + i));
+}
+
+__device__ __forceinline__ void store_one(void* p, long long i, float v, int st) {
+  if (st == FFST_STORE_F32) __stcs(static_cast<float*>(p) + i, v);
+  else if (st == FFST_STORE_F16) __stcs(static_cast<__half*>(p) + i, __float2half_rn(v));
+  else __stcs(static_cast<__nv_bfloat16*>(p) + i, __float2bfloat16_rn(v));
+}
+
+// r in the cyclic row interval (start rg.x, length rg.y) of a column of height n.
+__device__ __forceinline__ bool in_cyclic(int r, int2 rg, int n) {
+  int q = r - rg.x;
+  if (q < 0) q += n;
+  return q < rg.y;
+}
+
+// DFT (INV: unnormalised inverse DFT) of length b.n of the line whose
+// element j = t + T m (j < b.n; the rest is ignored) thread t holds in v[m];
+// on return v[m] holds output k = t + T m (zero for k >= b.n).  Every thread
+// of the block calls it (block barriers); it ends with a barrier after its
+// last read of `buf`.
+template <int L2, bool INV>
+__device__ __forceinline__ void blue_dft(float2 (&v)[ColCfg<L2>::E], float2* buf, int t, const BlueLine& b) {
+  constexpr int E = ColCfg<L2>::E, T = ColCfg<L2>::T;
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int j = t + T * m;
+    float2 x = v[m];
+    if (INV) x.y = -x.y;
+    v[m] = j < b.n ? cmul(x, __ldg(&b.chirp[j])) : make_float2(0.f, 0.f);
+  }
+  line_fft<L2, E, false, kSyncBlock>(v, buf, t, b.tw);
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = cmul(v[m], __ldg(&b.bhat[t + T * m]));
+  line_fft<L2, E, true, kSyncBlock>(v, buf, t, b.tw);
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = t + T * m;
+    float2 x = k < b.n ? cmul(v[m], __ldg(&b.chirp[k])) : make_float2(0.f, 0.f);
+    if (INV) x.y = -x.y;
+    v[m] = x;
+  }
+}
+
+#endif  // __CUDACC__
+
+}  // namespace ffst

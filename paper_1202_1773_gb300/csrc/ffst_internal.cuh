@@ -236,6 +236,15 @@ namespace ffst {
 // One launch per direction walks an ordered task queue; per-plane counters
 // carry the dependencies (rows of a plane after its columns, reuse of the
 // intermediate ring after its readers).
+// Tables of the generic-length lines of one dimension (ffst_blue.cuh).
+struct BlueLine {
+  int n = 0;                      // line length; 0: the dimension runs native FFT lines
+  int L2 = 0;                     // convolution length, the power of two >= 2n - 1
+  const float2* chirp = nullptr;  // w_j = exp(-i pi j^2 / n), j < n (FP64-generated)
+  const float2* bhat = nullptr;   // FFT_L2 of the filter conj(w_|m|), times 1/L2
+  const float2* tw = nullptr;     // pass table (L2, col_E(L2))
+};
+
 struct Sched {
   bool on = false;
   double ring_mb = 0.0;
@@ -276,6 +285,9 @@ struct ffst_plan_s {
   int inv_split = 1;                    // plane chunks per inverse group (partial accumulators)
   int inv_split_cap = 0;                // partial accumulators allocated
   int inv_split_default = 1;            // the plan's choice at creation
+  int P = 0;                            // columns per column-pass block (panel width)
+  ffst::BlueLine bl_rows, bl_cols;      // generic-length lines (n = 0: native FFT lines)
+  float2* d_blue = nullptr;             // their tables
   float* d_invD = nullptr;              // [M][Hc] 1 / sum_i psi_i^2 (FP32 psi), inverse normalisation
   float2* d_H = nullptr;                // two group intermediates (double buffer), h_elems each
   long long h_elems = 0;

@@ -7,7 +7,7 @@
 #include <cstring>
 #include <memory>
 
-#include "ffst_kernels.cuh"
+#include "ffst_blue.cuh"
 
 namespace ffst {
 
@@ -246,6 +246,7 @@ static void free_plan(ffst_plan_s* p) {
   cudaFree(p->d_tw_rows);
   cudaFree(p->d_tw_cols);
   cudaFree(p->d_rtw);
+  cudaFree(p->d_blue);
   cudaFree(p->d_rng);
   cudaFree(p->d_F);
   cudaFree(p->d_S);
@@ -350,7 +351,7 @@ static long long build_groups(const ffst_plan_s* p, double mb, std::vector<Group
 // directions and the double-buffered intermediate (sized for the larger
 // group of either direction).
 ffst_status plan_regroup(ffst_plan_s* p, double fwd_mb, double inv_mb) {
-  const int P = cols_per_cta(p->M);
+  const int P = p->P;
   cudaFree(p->d_items);
   cudaFree(p->d_partials);
   cudaFree(p->d_H);
@@ -410,7 +411,7 @@ static int default_inv_split(const ffst_plan_s* p) {
   }
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || sms < 1) sms = 1;
-  const int P = cols_per_cta(p->M);
+  const int P = p->P;
   const int npanels = (p->Hc + P - 1) / P;
   return std::max(1, std::min(kMaxInvSplit, 4 * sms / npanels));
 }
@@ -480,11 +481,16 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
   VSpec vs;
   if (vfun == FFST_V_POLY) vs = v_poly_spec(vorder);
   vs.kind = vfun;
-  if (rows < 8 || cols < 8 || rows > 4096 || cols > 4096 || rows % 2 || cols % 2 || !supported_line(rows) ||
-      !supported_line(cols / 2))
+  // native FFT lines: columns of length rows, rows as half-length complex
+  // lines of cols/2; any other length runs generic (Bluestein) lines of at
+  // most 2048 points
+  const bool nat_cols = rows >= 8 && rows <= 4096 && supported_line(rows);
+  const bool nat_rows = cols >= 8 && cols <= 4096 && cols % 2 == 0 && supported_line(cols / 2);
+  if (rows < 8 || cols < 8 || rows > 4096 || cols > 4096 || (!nat_cols && rows > kBlueMaxL2 / 2) ||
+      (!nat_rows && cols > kBlueMaxL2 / 2))
     return fail(FFST_ERR_UNSUPPORTED_SIZE,
-                "ffst_plan: rows must be a power of two in [8, 4096] or one of 240, 320, 384, 480, 640, 768, and "
-                "cols/2 a power of two in [4, 2048] or one of those, got " +
+                "ffst_plan: rows and cols must be in [8, 4096], and at most 2048 unless rows is a power of two or "
+                "one of 240, 320, 384, 480, 640, 768 (cols: twice one of those), got " +
                     std::to_string(rows) + "x" + std::to_string(cols));
   const int mx = rows > cols ? rows : cols;
   int lg = 0;
@@ -582,9 +588,45 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
   p->win.alp_row = p->win.alp_col + (size_t)j0 * ncol;
 
   // twiddles (FP64 -> FP32): row lines of length N/2, their real split, column lines of length M
-  if ((e = upload(&p->d_tw_rows, pass_table(cols / 2, row_E(cols / 2)))) != cudaSuccess) return cuda_fail(e, "twiddles");
-  if ((e = upload(&p->d_rtw, real_twiddles(cols))) != cudaSuccess) return cuda_fail(e, "twiddles");
-  if ((e = upload(&p->d_tw_cols, pass_table(rows, col_E(rows)))) != cudaSuccess) return cuda_fail(e, "twiddles");
+  if (nat_rows) {
+    if ((e = upload(&p->d_tw_rows, pass_table(cols / 2, row_E(cols / 2)))) != cudaSuccess) return cuda_fail(e, "twiddles");
+    if ((e = upload(&p->d_rtw, real_twiddles(cols))) != cudaSuccess) return cuda_fail(e, "twiddles");
+  }
+  if (nat_cols) {
+    if ((e = upload(&p->d_tw_cols, pass_table(rows, col_E(rows)))) != cudaSuccess) return cuda_fail(e, "twiddles");
+  }
+  // generic lines: chirp | filter spectrum | pass table, per generic dimension
+  {
+    std::vector<float2> tab;
+    size_t off[2][3] = {};
+    const int lens[2] = {nat_rows ? 0 : cols, nat_cols ? 0 : rows};
+    int L2s[2] = {0, 0};
+    for (int q = 0; q < 2; ++q) {
+      if (!lens[q]) continue;
+      std::vector<float2> chirp, bhat;
+      blue_tables(lens[q], &L2s[q], &chirp, &bhat);
+      const std::vector<float2> tw = pass_table(L2s[q], col_E(L2s[q]));
+      off[q][0] = tab.size();
+      tab.insert(tab.end(), chirp.begin(), chirp.end());
+      off[q][1] = tab.size();
+      tab.insert(tab.end(), bhat.begin(), bhat.end());
+      off[q][2] = tab.size();
+      tab.insert(tab.end(), tw.begin(), tw.end());
+    }
+    if (!tab.empty()) {
+      if ((e = upload(&p->d_blue, tab)) != cudaSuccess) return cuda_fail(e, "generic line tables");
+      BlueLine* bl[2] = {&p->bl_rows, &p->bl_cols};
+      for (int q = 0; q < 2; ++q) {
+        if (!lens[q]) continue;
+        bl[q]->n = lens[q];
+        bl[q]->L2 = L2s[q];
+        bl[q]->chirp = p->d_blue + off[q][0];
+        bl[q]->bhat = p->d_blue + off[q][1];
+        bl[q]->tw = p->d_blue + off[q][2];
+      }
+    }
+  }
+  p->P = nat_cols ? cols_per_cta(rows) : blue_lines_per_block(p->bl_cols.L2);
 
   // supports
   if ((e = cudaMalloc(&p->d_planes, p->planes.size() * sizeof(PlaneDesc))) != cudaSuccess)
@@ -639,8 +681,13 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
   if ((e = cudaMalloc(&p->d_err, sizeof(int))) != cudaSuccess || (e = cudaMemset(p->d_err, 0, sizeof(int))) != cudaSuccess)
     return cuda_fail(e, "error word");
   {
-    const int L = cols / 2, teams = kThreads / (L / row_E(L));
-    p->row_blocks = (rows + teams - 1) / teams;
+    if (nat_rows) {
+      const int L = cols / 2, teams = kThreads / (L / row_E(L));
+      p->row_blocks = (rows + teams - 1) / teams;
+    } else {  // generic row blocks take two rows per line
+      const int lines = blue_lines_per_block(p->bl_rows.L2);
+      p->row_blocks = ((rows + 1) / 2 + lines - 1) / lines;
+    }
     if ((e = cudaMalloc(&p->d_abs_partials, sizeof(float) * (size_t)p->eta * p->row_blocks)) != cudaSuccess)
       return cuda_fail(e, "statistics partials");
   }

@@ -1,0 +1,185 @@
+"""Generic sizes (odd, prime, and lengths without a native FFT line) against
+the FP64 oracle.
+
+A dimension whose length has no native line runs Bluestein lines: the DFT of
+length n as a chirp convolution through power-of-two FFTs of length
+L2 >= 2n - 1.  Everything after the line transforms (the Sec. 3.1 forward,
+the Sec. 3.3 inverse and adjoint, low-precision storage, the fused
+statistics and shrinkage, the one-sided complex shearlets of Sec. 3.8.2,
+the plane chunks of the inverse) is the same code as at native sizes, so the
+cases mix generic rows, generic columns and both.  Tolerances as in
+test_gpu_parity (relative L2): FP32 1e-5, FP16 2e-3, BF16 1e-2.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import ffst_oracle as o
+from paper_1202_1773_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+# (rows, cols): both generic, generic columns only, generic rows only,
+# primes, odd x even, the smallest size, and a mixed-radix native height
+SHAPES = [(8, 9), (15, 17), (63, 64), (64, 63), (100, 150), (131, 137), (127, 256), (256, 255), (240, 250),
+          (97, 480)]
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def ffst():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_1202_1773_gb300 as m
+
+    return m
+
+
+def _img(shape, seed):
+    return inputs.scaled_cartoon(*shape, seed=seed)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_forward_matches_oracle(ffst, shape):
+    f = _img(shape, 3)
+    p = ffst.Plan(*shape)
+    c = p.forward(torch.from_numpy(f).cuda()).cpu().numpy()
+    ref = o.forward(f.astype(np.float64))
+    assert c.shape == ref.shape
+    assert rel_l2(c, ref) <= FP32_TOL
+    p.close()
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_inverse_and_adjoint_match_oracle(ffst, shape):
+    eta = o.num_planes(o.default_scales(*shape))
+    cnp = np.random.default_rng(shape[0] * 7 + shape[1]).standard_normal((eta,) + shape).astype(np.float32)
+    p = ffst.Plan(*shape)
+    c = torch.from_numpy(cnp).cuda()
+    assert rel_l2(p.inverse(c).cpu().numpy(), o.inverse(cnp.astype(np.float64))) <= FP32_TOL
+    assert rel_l2(p.adjoint(c).cpu().numpy(), o.adjoint(cnp.astype(np.float64))) <= FP32_TOL
+    p.close()
+
+
+@pytest.mark.parametrize("shape", [(15, 17), (131, 137), (256, 255)])
+def test_reconstruction_and_parseval(ffst, shape):
+    f = _img(shape, 9)
+    p = ffst.Plan(*shape)
+    x = torch.from_numpy(f).cuda()
+    c = p.forward(x)
+    assert float(torch.linalg.norm(p.inverse(c) - x) / torch.linalg.norm(x)) <= FP32_TOL
+    assert float(torch.linalg.norm(p.adjoint(c) - x) / torch.linalg.norm(x)) <= FP32_TOL
+    # Parseval frame: sum_i ||c_i||^2 = ||f||^2
+    assert abs(float(torch.sum(c.double() ** 2)) / float(torch.sum(x.double() ** 2)) - 1.0) <= 2e-5
+    p.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [("f16", 2e-3), ("bf16", 1e-2)])
+def test_low_precision_storage(ffst, dtype, tol):
+    shape = (131, 137)
+    f = _img(shape, 4)
+    p = ffst.Plan(*shape)
+    x = torch.from_numpy(f).cuda()
+    dt = torch.float16 if dtype == "f16" else torch.bfloat16
+    c, sc = p.forward(x, dtype=dt)
+    got = (c.float() / sc.view(-1, 1, 1)).cpu().numpy()
+    ref = o.forward(f.astype(np.float64))
+    assert rel_l2(got, ref) <= tol
+    assert rel_l2(p.inverse(c, plane_scale=sc).cpu().numpy(), f) <= tol
+    p.close()
+
+
+def test_stats_and_shrinkage(ffst):
+    shape = (127, 129)
+    f = _img(shape, 21)
+    c_ref = o.forward(f.astype(np.float64))
+    p = ffst.Plan(*shape)
+    x = torch.from_numpy(f).cuda()
+    c, d = p.forward_stats(x)
+    d_ref = o.mean_abs(c_ref)
+    np.testing.assert_allclose(d.cpu().numpy(), d_ref, rtol=1e-5, atol=1e-7 * np.abs(d_ref).max())
+    assert torch.equal(c, p.forward(x))
+    tau = 0.8 * d_ref
+    tau[0] = 0.0
+    cs, _ = p.forward_stats(x, shrink="soft", thresh=torch.tensor(tau, dtype=torch.float32, device="cuda"))
+    want = o.shrink(c_ref, tau, "soft")
+    assert np.abs(cs.cpu().numpy() - want).max() <= 1e-5 * np.abs(c_ref).max()
+    p.close()
+
+
+@pytest.mark.parametrize("shape", [(63, 65), (100, 150)])
+def test_complex_matches_oracle(ffst, shape):
+    f = _img(shape, 8)
+    p = ffst.Plan(*shape)
+    x = torch.from_numpy(f).cuda()
+    z = p.forward_complex(x).cpu().numpy()
+    ref = o.forward_onesided(f.astype(np.float64), p.scales)
+    got = z[:, 0] + 1j * z[:, 1]
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= FP32_TOL
+    r = p.inverse_complex(torch.from_numpy(z).cuda())
+    assert float(torch.linalg.norm(r - x) / torch.linalg.norm(x)) <= FP32_TOL
+    p.close()
+
+
+def test_smooth_variant(ffst):
+    shape = (99, 101)
+    f = _img(shape, 2)
+    p = ffst.Plan(*shape, smooth=True)
+    c = p.forward(torch.from_numpy(f).cuda()).cpu().numpy()
+    assert rel_l2(c, o.forward(f.astype(np.float64), smooth=True)) <= FP32_TOL
+    p.close()
+
+
+@pytest.mark.parametrize("nsplit", [1, 3, 16])
+def test_inverse_chunks(ffst, nsplit):
+    shape = (131, 137)
+    eta = o.num_planes(o.default_scales(*shape))
+    cnp = np.random.default_rng(nsplit).standard_normal((eta,) + shape).astype(np.float32)
+    p = ffst.Plan(*shape)
+    p.inverse_split = nsplit
+    assert rel_l2(p.inverse(torch.from_numpy(cnp).cuda()).cpu().numpy(),
+                  o.inverse(cnp.astype(np.float64))) <= FP32_TOL
+    p.close()
+
+
+@pytest.mark.parametrize("shape,planes", [((1023, 1025), [0, 1, 7, 30, 60]), ((2047, 2048), [0, 13, 61, 124]),
+                                          ((1536, 2046), [0, 5, 62, 124])])
+def test_large_generic_sampled_planes(ffst, shape, planes):
+    # the largest generic lines (L2 = 4096): sampled planes against the oracle
+    # plane by plane, Parseval and reconstruction over the whole stack
+    f = _img(shape, 5)
+    p = ffst.Plan(*shape)
+    x = torch.from_numpy(f).cuda()
+    c = p.forward(x)
+    F = np.fft.fft2(f.astype(np.float64))
+    for i in planes:
+        ref = o.forward_plane(F, p.scales, i)
+        got = c[i].cpu().numpy()
+        err = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-3 * np.linalg.norm(f))
+        assert err <= FP32_TOL, (i, err)
+    energy = float(torch.sum(c.double() ** 2))
+    assert abs(energy / float(torch.sum(x.double() ** 2)) - 1.0) <= 2e-5
+    rec = p.inverse(c)
+    assert float(torch.linalg.norm(rec - x) / torch.linalg.norm(x)) <= FP32_TOL
+    p.close()
+
+
+def test_deterministic(ffst):
+    shape = (255, 257)
+    x = torch.from_numpy(_img(shape, 1)).cuda()
+    p = ffst.Plan(*shape)
+    c0 = p.forward(x).clone()
+    r0 = p.inverse(c0).clone()
+    for _ in range(2):
+        assert torch.equal(p.forward(x), c0)
+        assert torch.equal(p.inverse(c0), r0)
+    p.close()

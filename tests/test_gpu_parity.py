@@ -175,7 +175,7 @@ def test_errors_reported(ffst):
     from paper_1202_1773_gb300 import _lib
 
     with pytest.raises(ffst.FFSTError) as ei:
-        ffst.Plan(96, 64)
+        ffst.Plan(2049, 64)  # no native line and above the generic lines' 2048
     assert ei.value.status == _lib.FFST_ERR_UNSUPPORTED_SIZE
     plan = ffst.Plan(64, 64)
     x = torch.zeros(64, 64, device="cuda")
