@@ -471,6 +471,23 @@ def run_forms(plan, pool, stack, rec, plain_value, args, dev):
                      "accuracy": {"reconstruction_rel_l2": err}}
     sp.close()
 
+    # odd size: 2047x2047 (no native FFT line: Bluestein lines of L2 = 4096 in
+    # both dimensions), same scales, same round trip
+    on = ROWS - 1
+    op = ffst.Plan(on, on, SCALES, device=dev)
+    opool = [torch.from_numpy(inputs.scaled_cartoon(on, on, seed=400 + q)).to(dev) for q in range(2)]
+    ost = torch.empty(op.shape, device=dev)
+    orec = torch.empty(on, on, device=dev)
+    ms = _time_steps(lambda q: (op.forward(opool[q % 2], out=ost), op.inverse(ost, out=orec)), steps, dev)
+    op.forward(opool[0], out=ost)
+    err = float(torch.linalg.norm(op.inverse(ost) - opool[0]) / torch.linalg.norm(opool[0]))
+    ocps = op.num_planes * on * on
+    out["odd_2047"] = {"value": ocps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                       "vs_plain": ocps / (ms / 1e3) / plain_value, "size": f"{on}x{on}", "lines": "Bluestein, L2 = 4096",
+                       "accuracy": {"reconstruction_rel_l2": err}}
+    del ost, orec, opool
+    op.close()
+
     # batched: 256 images of uneven sizes, forward + inverse replayed from one CUDA graph
     del ref
     n = 256
@@ -505,7 +522,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the adjoint / f16 / bf16 / batched forms")
+    ap.add_argument("--no-forms", action="store_true", help="skip the adjoint / f16 / bf16 / stats / complex / smooth / odd-size / batched forms")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
