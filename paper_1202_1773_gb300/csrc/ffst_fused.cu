@@ -66,7 +66,7 @@ static cudaError_t inv_fused_M(const R2CArgs& ra, int nplanes, const InvColsArgs
   return cudaGetLastError();
 }
 
-bool fused_supported(int M, int N) { return M == N && M >= 256 && M <= 4096; }
+bool fused_supported(int M, int N) { return M == N && M >= 256 && M <= 4096 && (M & (M - 1)) == 0; }
 
 #define FFST_DISPATCH_FUSED(M, CALL)        \
   switch (M) {                              \

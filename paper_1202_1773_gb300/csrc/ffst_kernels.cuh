@@ -660,8 +660,8 @@ cudaError_t launch_cols_fft(int L, float2* buf, int width, int ld, bool inverse,
                             const float2* tw, cudaStream_t s, int nsum = 1, long long sstride = 0);
 cudaError_t launch_fwd_cols(int L, const FwdColsArgs& a, int nitems, cudaStream_t s);
 cudaError_t launch_inv_cols(int L, const InvColsArgs& a, cudaStream_t s);  // a.npanels x a.nchunks blocks
-// Fused launches exist for square images with 256 <= M <= 4096 (fused_supported);
-// other sizes return cudaErrorNotSupported and use the standalone kernels.
+// Fused launches exist for square power-of-two images with 256 <= M <= 4096
+// (fused_supported); other sizes run the standalone kernels.
 bool fused_supported(int M, int N);
 // Persistent schedule (ffst_sched.cu): one launch for all plane passes of a
 // forward (column items + row C2R) or an inverse (row R2C + column panels).

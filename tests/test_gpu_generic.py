@@ -173,6 +173,38 @@ def test_large_generic_sampled_planes(ffst, shape, planes):
     p.close()
 
 
+@pytest.mark.parametrize("n", [257, 384, 480])
+def test_square_sizes_without_fused_launches(ffst, n):
+    # square sizes whose lines are generic (257) or mixed-radix (384, 480) run
+    # the standalone passes; the fused launches are for powers of two only
+    shape = (n, n)
+    f = _img(shape, 12)
+    p = ffst.Plan(*shape)
+    x = torch.from_numpy(f).cuda()
+    c = p.forward(x)
+    assert rel_l2(c.cpu().numpy(), o.forward(f.astype(np.float64))) <= FP32_TOL
+    assert float(torch.linalg.norm(p.inverse(c) - x) / torch.linalg.norm(x)) <= FP32_TOL
+    p.schedule = 1  # no persistent schedule either
+    assert p.schedule == 0
+    p.close()
+
+
+def test_odd_square_2047_sampled_planes(ffst):
+    # the bench's odd-size form: Bluestein lines of L2 = 4096 in both dimensions
+    shape = (2047, 2047)
+    f = _img(shape, 5)
+    p = ffst.Plan(*shape)
+    x = torch.from_numpy(f).cuda()
+    c = p.forward(x)
+    F = np.fft.fft2(f.astype(np.float64))
+    for i in (0, 2, 62, 124):
+        ref = o.forward_plane(F, p.scales, i)
+        err = np.linalg.norm(c[i].cpu().numpy() - ref) / max(np.linalg.norm(ref), 1e-3 * np.linalg.norm(f))
+        assert err <= FP32_TOL, (i, err)
+    assert float(torch.linalg.norm(p.inverse(c) - x) / torch.linalg.norm(x)) <= FP32_TOL
+    p.close()
+
+
 def test_deterministic(ffst):
     shape = (255, 257)
     x = torch.from_numpy(_img(shape, 1)).cuda()
