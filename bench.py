@@ -156,6 +156,12 @@ def _max_over_ranks(x: float, world: int, device):
     return float(t.item())
 
 
+def _job_value(units_per_step: float, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units every rank processed (each rank runs
+    its own replica of the workload) over the slowest rank's time."""
+    return units_per_step * steps * world / (ms_max / 1e3)
+
+
 def _barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -270,7 +276,7 @@ def run_gpu(args):
     clocks = sampler.stop() if sampler else None
     ms = t0.elapsed_time(t1)
     ms_max = _max_over_ranks(ms, world, dev)
-    value = coeffs_per_step * args.steps * world / (ms_max / 1e3)
+    value = _job_value(coeffs_per_step, args.steps, world, ms_max)
 
     # the same number of steps again with every kernel bracketed by CUDA
     # events on the launch stream: per-kernel durations for the roofline
@@ -319,7 +325,7 @@ def run_gpu(args):
     b.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = _max_over_ranks(a.elapsed_time(b), world, dev)
-    e2e_value = coeffs_per_step * args.steps * world / (e2e_ms / 1e3)
+    e2e_value = _job_value(coeffs_per_step, args.steps, world, e2e_ms)
 
     forms = None if args.no_forms else run_forms(plan, pool, stack, rec, value, args, dev)
 
