@@ -45,14 +45,16 @@ UNIT = "coeffs/s"
 def _measured_traffic(kind):
     """DRAM bytes per launch of a kernel kind from the committed ncu capture
     (profiles/ffst_2048x2048_j5_dram_traffic.json), or None when the kernel
-    sources changed since that capture."""
+    sources changed since that capture.  The generic-length (Bluestein) line
+    sources, ffst_blue*, do not enter the native kernels and are left out."""
     import glob
     import hashlib
 
     try:
         with open(os.path.join(ROOT, "profiles", "ffst_2048x2048_j5_dram_traffic.json")) as fh:
             d = json.load(fh)
-        src = sorted(glob.glob(os.path.join(ROOT, "paper_1202_1773_gb300", "csrc", "*")) +
+        src = sorted([f for f in glob.glob(os.path.join(ROOT, "paper_1202_1773_gb300", "csrc", "*"))
+                      if not os.path.basename(f).startswith("ffst_blue")] +
                      glob.glob(os.path.join(ROOT, "include", "*.h")))
         h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
         if h != d["source_hash"]:

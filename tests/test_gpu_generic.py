@@ -215,3 +215,30 @@ def test_deterministic(ffst):
         assert torch.equal(p.forward(x), c0)
         assert torch.equal(p.inverse(c0), r0)
     p.close()
+
+
+def test_batched_and_graph_at_generic_sizes(ffst):
+    # uneven batches mixing native and generic sizes over lane streams, eager
+    # and replayed from one CUDA graph, against single plans bit for bit
+    shapes = [(63, 65), (100, 150), (64, 64), (131, 137), (63, 65), (256, 255)]
+    imgs = [torch.from_numpy(_img(sh, 40 + i)).cuda() for i, sh in enumerate(shapes)]
+    bp = ffst.BatchPlan(shapes, lanes=3)
+    stacks = bp.forward(imgs)
+    recs = bp.inverse(stacks)
+    torch.cuda.synchronize()
+    for i, sh in enumerate(shapes):
+        p = ffst.Plan(*sh)
+        ref = p.forward(imgs[i])
+        assert torch.equal(stacks[i], ref), i
+        assert torch.equal(recs[i], p.inverse(ref)), i
+        p.close()
+    gst = bp.empty_stacks()
+    outs = [torch.empty_like(x) for x in imgs]
+    g = bp.capture(imgs, gst, outs, what=3)
+    g.launch()
+    torch.cuda.synchronize()
+    for i in range(len(bp)):
+        assert torch.equal(gst[i], stacks[i]), i
+        assert torch.equal(outs[i], recs[i]), i
+    g.close()
+    bp.close()
