@@ -28,6 +28,22 @@ namespace ffst {
 constexpr int kBlueMinL2 = 16;
 constexpr int kBlueMaxL2 = 4096;  // lines up to n = 2048
 
+// Elements per thread of a generic line: as the native column lines, but at
+// most 16, so that the two FFTs of a Bluestein line keep the register
+// footprint of the native kernels (a 4096-point line is one team of 256
+// threads).  The host builds the pass tables with the same E.
+__host__ __device__ constexpr int blue_E(int L2) { return col_E(L2) < 16 ? col_E(L2) : 16; }
+
+template <int L2>
+struct BlueCfg {
+  static constexpr int E = blue_E(L2);
+  static constexpr int T = L2 / E;
+  static constexpr int P = kThreads / T;  // lines per block
+  static constexpr int BUF = team_stride(L2, E, P >= 16 ? 1 : 16 / P);
+  static constexpr size_t SMEM = sizeof(float2) * P * BUF;
+  static_assert(P * T == kThreads, "generic line teams must fill the block");
+};
+
 // Columns (lines) per block of the generic column (row) passes.
 int blue_lines_per_block(int L2);
 
@@ -72,8 +88,8 @@ __device__ __forceinline__ bool in_cyclic(int r, int2 rg, int n) {
 // of the block calls it (block barriers); it ends with a barrier after its
 // last read of `buf`.
 template <int L2, bool INV>
-__device__ __forceinline__ void blue_dft(float2 (&v)[ColCfg<L2>::E], float2* buf, int t, const BlueLine& b) {
-  constexpr int E = ColCfg<L2>::E, T = ColCfg<L2>::T;
+__device__ __forceinline__ void blue_dft(float2 (&v)[BlueCfg<L2>::E], float2* buf, int t, const BlueLine& b) {
+  constexpr int E = BlueCfg<L2>::E, T = BlueCfg<L2>::T;
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int j = t + T * m;

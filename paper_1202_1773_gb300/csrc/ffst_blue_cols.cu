@@ -9,10 +9,10 @@ namespace ffst {
 // buf, after summing nsum partial arrays and scaling by scale_tab (as
 // cols_fft_body).
 template <int L2, bool INV>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
     k_blue_cols(float2* __restrict__ buf, int width, int ld, const float* __restrict__ scale_tab, int nsum,
                 long long sstride, BlueLine b) {
-  constexpr int E = ColCfg<L2>::E, T = ColCfg<L2>::T, P = ColCfg<L2>::P;
+  constexpr int E = BlueCfg<L2>::E, T = BlueCfg<L2>::T, P = BlueCfg<L2>::P;
   extern __shared__ __align__(128) float2 smem[];
   const int t = threadIdx.x / P, cl = threadIdx.x % P;
   const int c = blockIdx.x * P + cl;
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     v[m] = x;
   }
-  blue_dft<L2, INV>(v, smem + cl * ColCfg<L2>::BUF, t, b);
+  blue_dft<L2, INV>(v, smem + cl * BlueCfg<L2>::BUF, t, b);
   if (act) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -49,12 +49,12 @@ __global__ void __launch_bounds__(kThreads, 2)
 // plane's slot, and the item's sum |G| (each column counted for itself and
 // its conjugate partner) as fwd_cols_body.
 template <int L2>
-__global__ void __launch_bounds__(kThreads, 2) k_blue_fwd_cols(FwdColsArgs a, BlueLine b) {
-  constexpr int E = ColCfg<L2>::E, T = ColCfg<L2>::T, P = ColCfg<L2>::P;
+__global__ void __launch_bounds__(kThreads, 3) k_blue_fwd_cols(FwdColsArgs a, BlueLine b) {
+  constexpr int E = BlueCfg<L2>::E, T = BlueCfg<L2>::T, P = BlueCfg<L2>::P;
   extern __shared__ __align__(128) float2 smem[];
   __shared__ float red[kThreads / 32];
   const int t = threadIdx.x / P, cl = threadIdx.x % P;
-  float2* buf = smem + cl * ColCfg<L2>::BUF;
+  float2* buf = smem + cl * BlueCfg<L2>::BUF;
   const int item = blockIdx.x;
   const int n = b.n;
   const ColItem it = a.items[item];
@@ -113,11 +113,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_blue_fwd_cols(FwdColsArgs a, Bl
 // spectra and S += psi_hat_i * (that) on the column's support rows, in plane
 // order (each S element belongs to one thread: deterministic).
 template <int L2>
-__global__ void __launch_bounds__(kThreads, 2) k_blue_inv_cols(InvColsArgs a, BlueLine b) {
-  constexpr int E = ColCfg<L2>::E, T = ColCfg<L2>::T, P = ColCfg<L2>::P;
+__global__ void __launch_bounds__(kThreads, 3) k_blue_inv_cols(InvColsArgs a, BlueLine b) {
+  constexpr int E = BlueCfg<L2>::E, T = BlueCfg<L2>::T, P = BlueCfg<L2>::P;
   extern __shared__ __align__(128) float2 smem[];
   const int t = threadIdx.x / P, cl = threadIdx.x % P;
-  float2* buf = smem + cl * ColCfg<L2>::BUF;
+  float2* buf = smem + cl * BlueCfg<L2>::BUF;
   const int n = b.n;
   int q0, q1;
   float2* S;
@@ -160,16 +160,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_blue_inv_cols(InvColsArgs a, Bl
 template <int L2>
 static cudaError_t cols_L2(const BlueLine& b, float2* buf, int width, int ld, bool inverse, const float* scale_tab,
                            int nsum, long long sstride, cudaStream_t s) {
-  constexpr int P = ColCfg<L2>::P;
+  constexpr int P = BlueCfg<L2>::P;
   const int grid = (width + P - 1) / P;
   if (grid <= 0) return cudaSuccess;
   cudaError_t e;
   if (inverse) {
-    if ((e = set_smem(k_blue_cols<L2, true>, ColCfg<L2>::SMEM)) != cudaSuccess) return e;
-    k_blue_cols<L2, true><<<grid, kThreads, ColCfg<L2>::SMEM, s>>>(buf, width, ld, scale_tab, nsum, sstride, b);
+    if ((e = set_smem(k_blue_cols<L2, true>, BlueCfg<L2>::SMEM)) != cudaSuccess) return e;
+    k_blue_cols<L2, true><<<grid, kThreads, BlueCfg<L2>::SMEM, s>>>(buf, width, ld, scale_tab, nsum, sstride, b);
   } else {
-    if ((e = set_smem(k_blue_cols<L2, false>, ColCfg<L2>::SMEM)) != cudaSuccess) return e;
-    k_blue_cols<L2, false><<<grid, kThreads, ColCfg<L2>::SMEM, s>>>(buf, width, ld, scale_tab, nsum, sstride, b);
+    if ((e = set_smem(k_blue_cols<L2, false>, BlueCfg<L2>::SMEM)) != cudaSuccess) return e;
+    k_blue_cols<L2, false><<<grid, kThreads, BlueCfg<L2>::SMEM, s>>>(buf, width, ld, scale_tab, nsum, sstride, b);
   }
   return cudaGetLastError();
 }
@@ -177,9 +177,9 @@ static cudaError_t cols_L2(const BlueLine& b, float2* buf, int width, int ld, bo
 template <int L2>
 static cudaError_t fwd_cols_L2(const BlueLine& b, const FwdColsArgs& a, int nitems, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
-  cudaError_t e = set_smem(k_blue_fwd_cols<L2>, ColCfg<L2>::SMEM);
+  cudaError_t e = set_smem(k_blue_fwd_cols<L2>, BlueCfg<L2>::SMEM);
   if (e != cudaSuccess) return e;
-  k_blue_fwd_cols<L2><<<nitems, kThreads, ColCfg<L2>::SMEM, s>>>(a, b);
+  k_blue_fwd_cols<L2><<<nitems, kThreads, BlueCfg<L2>::SMEM, s>>>(a, b);
   return cudaGetLastError();
 }
 
@@ -187,9 +187,9 @@ template <int L2>
 static cudaError_t inv_cols_L2(const BlueLine& b, const InvColsArgs& a, cudaStream_t s) {
   const int nb = a.npanels * a.nchunks;
   if (nb <= 0) return cudaSuccess;
-  cudaError_t e = set_smem(k_blue_inv_cols<L2>, ColCfg<L2>::SMEM);
+  cudaError_t e = set_smem(k_blue_inv_cols<L2>, BlueCfg<L2>::SMEM);
   if (e != cudaSuccess) return e;
-  k_blue_inv_cols<L2><<<nb, kThreads, ColCfg<L2>::SMEM, s>>>(a, b);
+  k_blue_inv_cols<L2><<<nb, kThreads, BlueCfg<L2>::SMEM, s>>>(a, b);
   return cudaGetLastError();
 }
 

@@ -56,15 +56,15 @@ void blue_tables(int n, int* L2out, std::vector<float2>* chirp, std::vector<floa
 
 int blue_lines_per_block(int L2) {
   switch (L2) {
-    case 16: return ColCfg<16>::P;
-    case 32: return ColCfg<32>::P;
-    case 64: return ColCfg<64>::P;
-    case 128: return ColCfg<128>::P;
-    case 256: return ColCfg<256>::P;
-    case 512: return ColCfg<512>::P;
-    case 1024: return ColCfg<1024>::P;
-    case 2048: return ColCfg<2048>::P;
-    case 4096: return ColCfg<4096>::P;
+    case 16: return BlueCfg<16>::P;
+    case 32: return BlueCfg<32>::P;
+    case 64: return BlueCfg<64>::P;
+    case 128: return BlueCfg<128>::P;
+    case 256: return BlueCfg<256>::P;
+    case 512: return BlueCfg<512>::P;
+    case 1024: return BlueCfg<1024>::P;
+    case 2048: return BlueCfg<2048>::P;
+    case 4096: return BlueCfg<4096>::P;
     default: return 0;
   }
 }
@@ -77,11 +77,11 @@ int blue_lines_per_block(int L2) {
 // the native row pass).
 // ---------------------------------------------------------------------------
 template <int L2>
-__global__ void __launch_bounds__(kThreads, 2) k_blue_rows_r2c(R2CArgs a, BlueLine b) {
-  constexpr int E = ColCfg<L2>::E, T = ColCfg<L2>::T, P = ColCfg<L2>::P;
+__global__ void __launch_bounds__(kThreads, 3) k_blue_rows_r2c(R2CArgs a, BlueLine b) {
+  constexpr int E = BlueCfg<L2>::E, T = BlueCfg<L2>::T, P = BlueCfg<L2>::P;
   extern __shared__ __align__(128) float2 smem[];
   const int team = threadIdx.x / T, t = threadIdx.x % T;
-  float2* buf = smem + team * ColCfg<L2>::BUF;
+  float2* buf = smem + team * BlueCfg<L2>::BUF;
   const int n = b.n;
   const int by = blockIdx.y, plane = a.plane0 + by;
   const int r0 = 2 * (blockIdx.x * P + team), r1 = r0 + 1;
@@ -136,12 +136,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_blue_rows_r2c(R2CArgs a, BlueLi
 // scale * s_i, per-plane statistics and shrinkage, storage.
 // ---------------------------------------------------------------------------
 template <int L2>
-__global__ void __launch_bounds__(kThreads, 2) k_blue_rows_c2r(C2RArgs a, BlueLine b) {
-  constexpr int E = ColCfg<L2>::E, T = ColCfg<L2>::T, P = ColCfg<L2>::P;
+__global__ void __launch_bounds__(kThreads, 3) k_blue_rows_c2r(C2RArgs a, BlueLine b) {
+  constexpr int E = BlueCfg<L2>::E, T = BlueCfg<L2>::T, P = BlueCfg<L2>::P;
   extern __shared__ __align__(128) float2 smem[];
   __shared__ float red[kThreads / 32];
   const int team = threadIdx.x / T, t = threadIdx.x % T;
-  float2* buf = smem + team * ColCfg<L2>::BUF;
+  float2* buf = smem + team * BlueCfg<L2>::BUF;
   const int n = b.n;
   const int by = blockIdx.y, plane = a.plane0 + by;
   const int r0 = 2 * (blockIdx.x * P + team), r1 = r0 + 1;
@@ -224,23 +224,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_blue_rows_c2r(C2RArgs a, BlueLi
 
 template <int L2>
 static cudaError_t rows_r2c_L2(const BlueLine& b, const R2CArgs& a, int nplanes, cudaStream_t s) {
-  constexpr int P = ColCfg<L2>::P;
+  constexpr int P = BlueCfg<L2>::P;
   const dim3 grid((unsigned)(((a.M + 1) / 2 + P - 1) / P), (unsigned)nplanes);
   if (nplanes <= 0 || a.M <= 0) return cudaSuccess;
-  cudaError_t e = set_smem(k_blue_rows_r2c<L2>, ColCfg<L2>::SMEM);
+  cudaError_t e = set_smem(k_blue_rows_r2c<L2>, BlueCfg<L2>::SMEM);
   if (e != cudaSuccess) return e;
-  k_blue_rows_r2c<L2><<<grid, kThreads, ColCfg<L2>::SMEM, s>>>(a, b);
+  k_blue_rows_r2c<L2><<<grid, kThreads, BlueCfg<L2>::SMEM, s>>>(a, b);
   return cudaGetLastError();
 }
 
 template <int L2>
 static cudaError_t rows_c2r_L2(const BlueLine& b, const C2RArgs& a, int nplanes, cudaStream_t s) {
-  constexpr int P = ColCfg<L2>::P;
+  constexpr int P = BlueCfg<L2>::P;
   const dim3 grid((unsigned)(((a.M + 1) / 2 + P - 1) / P), (unsigned)nplanes);
   if (nplanes <= 0 || a.M <= 0) return cudaSuccess;
-  cudaError_t e = set_smem(k_blue_rows_c2r<L2>, ColCfg<L2>::SMEM);
+  cudaError_t e = set_smem(k_blue_rows_c2r<L2>, BlueCfg<L2>::SMEM);
   if (e != cudaSuccess) return e;
-  k_blue_rows_c2r<L2><<<grid, kThreads, ColCfg<L2>::SMEM, s>>>(a, b);
+  k_blue_rows_c2r<L2><<<grid, kThreads, BlueCfg<L2>::SMEM, s>>>(a, b);
   return cudaGetLastError();
 }
 

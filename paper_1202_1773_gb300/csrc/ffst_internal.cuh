@@ -242,7 +242,7 @@ struct BlueLine {
   int L2 = 0;                     // convolution length, the power of two >= 2n - 1
   const float2* chirp = nullptr;  // w_j = exp(-i pi j^2 / n), j < n (FP64-generated)
   const float2* bhat = nullptr;   // FFT_L2 of the filter conj(w_|m|), times 1/L2
-  const float2* tw = nullptr;     // pass table (L2, col_E(L2))
+  const float2* tw = nullptr;     // pass table (L2, blue_E(L2))
 };
 
 struct Sched {

@@ -605,7 +605,7 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
       if (!lens[q]) continue;
       std::vector<float2> chirp, bhat;
       blue_tables(lens[q], &L2s[q], &chirp, &bhat);
-      const std::vector<float2> tw = pass_table(L2s[q], col_E(L2s[q]));
+      const std::vector<float2> tw = pass_table(L2s[q], blue_E(L2s[q]));
       off[q][0] = tab.size();
       tab.insert(tab.end(), chirp.begin(), chirp.end());
       off[q][1] = tab.size();
