@@ -85,10 +85,16 @@ def _storage_of(dtype) -> int:
 class Plan:
     """A libffst plan for rows x cols float32 images on one CUDA device.
 
+    Sizes 8..4096 per side.  Heights that are powers of two or 240, 320,
+    384, 480, 640, 768 (widths: twice one of those) run native FFT lines;
+    any other length up to 2048 (odd and prime included) runs Bluestein
+    lines.  Square powers of two from 256 use the fused plane passes.
+
     Construction options (ffst_plan_ex): smooth=True builds the smooth
     shearlets of Sec. 3.4; vfun picks the auxiliary function v ("meyer",
     "quadratic", ("poly", k) or "cinf"); max_scale="min" uses the smaller
-    grid extent X = 2^{2 j0 - 2}.
+    grid extent X = 2^{2 j0 - 2}.  ``inverse_split`` sets the plane chunks
+    of the inverse's sum (ffst_plan_set_inverse_split).
     """
 
     _VFUNS = {"meyer": _lib.FFST_V_MEYER, "quadratic": _lib.FFST_V_QUADRATIC, "cinf": _lib.FFST_V_CINF}
