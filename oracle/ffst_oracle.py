@@ -29,9 +29,11 @@ in the project's design notes):
 
 * axis: omega_1 runs along columns (x), omega_2 along rows (y); the
   coefficient stack is stored as ``[eta, M, N]`` (plane-major);
-* grid: each axis spans [-X, X] with its own spacing, xi = omega * X /
-  floor(L/2) (the paper's odd-size symmetric linspace, padded by one sample
-  for even sizes and the last sample dropped, written as a product);
+* grid: one step Delta = X / floor(max(M, N)/2) for both axes, xi = Delta *
+  omega (the paper's odd-size symmetric linspace of the larger dimension,
+  padded by one sample for even sizes and the last sample dropped, written
+  as a product), so the lattice lies in [-Y, Y] x [-X, X] with Y <= X; the
+  option ``spacing="per_axis"`` stretches each axis to [-X, X] instead;
 * cone membership is decided exactly on the integer frequency indices;
 * the Nyquist fix replaces psi(w1, -M/2) by sqrt((psi(w1)^2 + psi(-w1)^2)/2)
   (same for the column -N/2), which reproduces the paper's mirroring example
@@ -39,9 +41,11 @@ in the project's design notes):
 
 Pins: every function here is checked in ``tests/test_oracle_*.py`` against
 closed forms, the paper's lemmas/theorems, printed tables and worked
-examples, brute-force DFTs and invariants.  No function is "parity unpinned"
-except ``spectrum`` for non-square sizes, where the paper does not fix the
-grid (see the reading above); square sizes are pinned by transpose symmetry.
+examples, brute-force DFTs and invariants.  Square spectra are pinned by
+transpose symmetry and the window pins; non-square spectra of the default
+grid are pinned to the square ones (with one step Delta the M x N lattice is
+a window of the max x max lattice), and the Sec. 3.5.1 statements that
+single out that grid (one Delta, 1/4 < Delta <= 1, X >= Y) are tested.
 """
 
 from __future__ import annotations
@@ -218,45 +222,77 @@ def freq_index(L: int) -> np.ndarray:
     return np.where(p < half, p, p - L)
 
 
-def grid_spacing(L: int, scales: int, max_scale: str = "max") -> float:
-    """Grid step of one axis of Xi, Sec. 3.5.1: X / floor(L/2).
+def grid_extent(scales: int, max_scale: str = "max") -> float:
+    """Largest grid value X, Sec. 3.5.1: X = 2^{2 j0 - 1} (the paper's choice X_3,
+    the largest finest scale, its option maxScale = 'max') or X = 2^{2 j0 - 2}
+    (X_2, the smallest reasonable finest scale, maxScale = 'min'); Sec. 3.5.1
+    allows any X between the two."""
+    if max_scale not in ("max", "min"):
+        raise ValueError(f"max_scale must be 'max' or 'min', not {max_scale!r}")
+    return 2.0 ** (2 * scales - (1 if max_scale == "max" else 2))
 
-    X = 2^{2 j0 - 1} (the paper's choice X_3, the largest finest scale, its
-    option maxScale = 'max') or X = 2^{2 j0 - 2} (X_2, the smallest reasonable
-    finest scale, maxScale = 'min'); Sec. 3.5.1 allows any X between the two.
+
+def grid_spacing(L: int, scales: int, max_scale: str = "max") -> float:
+    """Grid step Delta for a dimension of length L spanning [-X, X], Sec. 3.5.1:
+    X / floor(L/2).
+
     For odd L the paper's grid is linspace(-X, X, L), step 2X/(L-1) =
     X/floor(L/2); for even L it pads to L+1 and drops the last sample,
     which keeps the same step.
     """
-    if max_scale not in ("max", "min"):
-        raise ValueError(f"max_scale must be 'max' or 'min', not {max_scale!r}")
-    X = 2.0 ** (2 * scales - (1 if max_scale == "max" else 2))
+    X = grid_extent(scales, max_scale)
     h = L // 2
     if h == 0:
         return 0.0
     return X / h
 
 
-def grid(rows: int, cols: int, scales: int, max_scale: str = "max"):
+SPACINGS = ("common", "per_axis")
+
+
+def grid_denominators(rows: int, cols: int, spacing: str = "common"):
+    """Integer denominators (g_m, g_n) of the grid: xi2 = o2 X / g_m, xi1 = o1 X / g_n.
+
+    "common" (default): Sec. 3.5.1 derives one step Delta from the larger
+    dimension, N = max(M, N) ("without loss of generality"): both axes use
+    Delta = X / floor(max(M, N)/2), so the lattice is Xi in [-Y, Y] x [-X, X]
+    with Y = Delta floor(min(M, N)/2) <= X, the paper's "X >= Y", and Xi =
+    Delta * Omega, the paper's remark that psi(Delta omega) on Omega gives the
+    same spectra.  "per_axis": each axis spans [-X, X] with its own step
+    X / floor(L/2) (Y = X).  Both are Parseval frames; they coincide for
+    square images.
+    """
+    if spacing == "common":
+        g = max(rows, cols) // 2
+        return g, g
+    if spacing == "per_axis":
+        return rows // 2, cols // 2
+    raise ValueError(f"spacing must be one of {SPACINGS}, not {spacing!r}")
+
+
+def grid(rows: int, cols: int, scales: int, max_scale: str = "max", spacing: str = "common"):
     """Integer indices (o1, o2) and grid points (xi1, xi2), shape (M, N).
 
     xi1 (omega_1) varies along columns, xi2 (omega_2) along rows.
     """
+    gm, gn = grid_denominators(rows, cols, spacing)
+    X = grid_extent(scales, max_scale)
     o1 = freq_index(cols)[None, :] * np.ones((rows, 1), dtype=np.int64)
     o2 = freq_index(rows)[:, None] * np.ones((1, cols), dtype=np.int64)
-    xi1 = o1 * grid_spacing(cols, scales, max_scale)
-    xi2 = o2 * grid_spacing(rows, scales, max_scale)
+    xi1 = o1 * (X / gn)
+    xi2 = o2 * (X / gm)
     return o1, o2, xi1, xi2
 
 
-def cones(rows: int, cols: int, o1, o2):
+def cones(rows: int, cols: int, o1, o2, spacing: str = "common"):
     """Masks of C^h, C^v and the seam lines C^x on the grid, Sec. 2.3.
 
-    |xi2| < |xi1|  <=>  |o2| * floor(N/2) < |o1| * floor(M/2), decided in
-    integers.  The origin belongs to none of them.
+    |xi2| < |xi1|  <=>  |o2| g_n < |o1| g_m (see ``grid_denominators``),
+    decided in integers.  The origin belongs to none of them.
     """
-    lhs = np.abs(o2) * (cols // 2)
-    rhs = np.abs(o1) * (rows // 2)
+    gm, gn = grid_denominators(rows, cols, spacing)
+    lhs = np.abs(o2) * gn
+    rhs = np.abs(o1) * gm
     nonzero = (o1 != 0) | (o2 != 0)
     ch = (lhs < rhs) & nonzero
     cv = (lhs > rhs) & nonzero
@@ -276,7 +312,7 @@ def _ratio(num, den, mask):
 
 
 def spectrum_raw(rows: int, cols: int, scales: int, i: int, smooth: bool = False, vfun="meyer",
-                 max_scale: str = "max") -> np.ndarray:
+                 max_scale: str = "max", spacing: str = "common") -> np.ndarray:
     """Spectrum of plane i on Xi without the Nyquist fix, FFT storage order.
 
     Sec. 3.1 eq. (shearletTransform):
@@ -289,13 +325,14 @@ def spectrum_raw(rows: int, cols: int, scales: int, i: int, smooth: bool = False
     radial factor of both cones is Psi1_hat(4^-j xi) (eq. newPsi1) and the
     low-pass is the tensor product Phi_hat(xi) (Sec. 2.4 eq. Phi).  vfun
     selects the auxiliary function v of every window (see ``v``), max_scale
-    the grid extent X (see ``grid_spacing``).
+    the grid extent X (see ``grid_extent``), spacing the grid step of a
+    non-square image (see ``grid_denominators``).
     """
     kappa, j, k = plane_table(scales)[i]
-    o1, o2, xi1, xi2 = grid(rows, cols, scales, max_scale)
+    o1, o2, xi1, xi2 = grid(rows, cols, scales, max_scale, spacing)
     if kappa == "lowpass":
         return Phi_hat(xi1, xi2, vfun) if smooth else phi_hat(xi1, xi2, vfun)
-    ch, cv, cx = cones(rows, cols, o1, o2)
+    ch, cv, cx = cones(rows, cols, o1, o2, spacing)
     a = 4.0 ** (-j)
     J = 2.0**j
     if smooth:
@@ -338,32 +375,32 @@ def nyquist_mirror(psi: np.ndarray) -> np.ndarray:
 
 
 def spectrum(rows: int, cols: int, scales: int, i: int, real_fix: bool = True, smooth: bool = False,
-             vfun="meyer", max_scale: str = "max") -> np.ndarray:
+             vfun="meyer", max_scale: str = "max", spacing: str = "common") -> np.ndarray:
     """Spectrum psi_hat_i of plane i (FFT storage order), fix applied by default.
 
     The fix is on by default, as the paper's ``realReal`` option (Sec. 3.5.3).
     """
-    raw = spectrum_raw(rows, cols, scales, i, smooth, vfun, max_scale)
+    raw = spectrum_raw(rows, cols, scales, i, smooth, vfun, max_scale, spacing)
     return nyquist_mirror(raw) if real_fix else raw
 
 
 def spectra(rows: int, cols: int, scales: int | None = None, real_fix: bool = True,
-            smooth: bool = False, vfun="meyer", max_scale: str = "max") -> np.ndarray:
+            smooth: bool = False, vfun="meyer", max_scale: str = "max", spacing: str = "common") -> np.ndarray:
     """Stack of all eta spectra, shape (eta, M, N), Sec. 3.5.2."""
     if scales is None:
         scales = default_scales(rows, cols)
-    return np.stack([spectrum(rows, cols, scales, i, real_fix, smooth, vfun, max_scale)
+    return np.stack([spectrum(rows, cols, scales, i, real_fix, smooth, vfun, max_scale, spacing)
                      for i in range(num_planes(scales))])
 
 
 def frame_sum(rows: int, cols: int, scales: int | None = None, real_fix: bool = True,
-              smooth: bool = False, vfun="meyer", max_scale: str = "max") -> np.ndarray:
+              smooth: bool = False, vfun="meyer", max_scale: str = "max", spacing: str = "common") -> np.ndarray:
     """sum_i psi_hat_i^2 on the grid (Sec. 3.6, frame tightness)."""
     if scales is None:
         scales = default_scales(rows, cols)
     acc = np.zeros((rows, cols))
     for i in range(num_planes(scales)):
-        acc += spectrum(rows, cols, scales, i, real_fix, smooth, vfun, max_scale) ** 2
+        acc += spectrum(rows, cols, scales, i, real_fix, smooth, vfun, max_scale, spacing) ** 2
     return acc
 
 
@@ -372,26 +409,28 @@ def frame_sum(rows: int, cols: int, scales: int | None = None, real_fix: bool = 
 # ---------------------------------------------------------------------------
 
 
-def forward_complex(f: np.ndarray, scales: int | None = None, real_fix: bool = True) -> np.ndarray:
+def forward_complex(f: np.ndarray, scales: int | None = None, real_fix: bool = True,
+                    spacing: str = "common") -> np.ndarray:
     """c_i = ifft2(psi_hat_i * fft2(f)) as complex numbers, Sec. 3.1 eq. (shearletTransform)."""
     f = np.asarray(f, dtype=np.float64)
     M, N = f.shape
     if scales is None:
         scales = default_scales(M, N)
     F = np.fft.fft2(f)
-    return np.stack([np.fft.ifft2(spectrum(M, N, scales, i, real_fix) * F)
+    return np.stack([np.fft.ifft2(spectrum(M, N, scales, i, real_fix, spacing=spacing) * F)
                      for i in range(num_planes(scales))])
 
 
 def forward_plane(F: np.ndarray, scales: int, i: int, smooth: bool = False, vfun="meyer",
-                  max_scale: str = "max") -> np.ndarray:
+                  max_scale: str = "max", spacing: str = "common") -> np.ndarray:
     """One real coefficient plane from a precomputed F = fft2(f)."""
     M, N = F.shape
-    return np.real(np.fft.ifft2(spectrum(M, N, scales, i, smooth=smooth, vfun=vfun, max_scale=max_scale) * F))
+    return np.real(np.fft.ifft2(spectrum(M, N, scales, i, smooth=smooth, vfun=vfun, max_scale=max_scale,
+                                         spacing=spacing) * F))
 
 
 def forward(f: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer",
-            max_scale: str = "max") -> np.ndarray:
+            max_scale: str = "max", spacing: str = "common") -> np.ndarray:
     """Real coefficient stack (eta, M, N): the real part of ``forward_complex``.
 
     With the Nyquist fix the imaginary part is rounding noise (Sec. 3.8.1).
@@ -401,11 +440,12 @@ def forward(f: np.ndarray, scales: int | None = None, smooth: bool = False, vfun
     if scales is None:
         scales = default_scales(M, N)
     F = np.fft.fft2(f)
-    return np.stack([forward_plane(F, scales, i, smooth, vfun, max_scale) for i in range(num_planes(scales))])
+    return np.stack([forward_plane(F, scales, i, smooth, vfun, max_scale, spacing)
+                     for i in range(num_planes(scales))])
 
 
 def adjoint(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer",
-            max_scale: str = "max") -> np.ndarray:
+            max_scale: str = "max", spacing: str = "common") -> np.ndarray:
     """T* c = Re ifft2( sum_i psi_hat_i * fft2(c_i) ), Sec. 3.3.
 
     For a Parseval frame T* = T^-1 (Sec. 3.2, eq. shearlet_transform_as_matrix).
@@ -416,12 +456,13 @@ def adjoint(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun
         scales = default_scales(M, N)
     acc = np.zeros((M, N), dtype=np.complex128)
     for i in range(num_planes(scales)):
-        acc += spectrum(M, N, scales, i, smooth=smooth, vfun=vfun, max_scale=max_scale) * np.fft.fft2(c[i])
+        acc += spectrum(M, N, scales, i, smooth=smooth, vfun=vfun, max_scale=max_scale,
+                        spacing=spacing) * np.fft.fft2(c[i])
     return np.real(np.fft.ifft2(acc))
 
 
 def inverse(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun="meyer",
-            max_scale: str = "max") -> np.ndarray:
+            max_scale: str = "max", spacing: str = "common") -> np.ndarray:
     """Re ifft2( sum_i psi_hat_i * fft2(c_i) / sum_i psi_hat_i^2 ), Sec. 3.3.
 
     Sec. 3.3 eq. (inverseShearletTransform) sums the products; the division
@@ -435,7 +476,7 @@ def inverse(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun
     acc = np.zeros((M, N), dtype=np.complex128)
     den = np.zeros((M, N))
     for i in range(num_planes(scales)):
-        s = spectrum(M, N, scales, i, smooth=smooth, vfun=vfun, max_scale=max_scale)
+        s = spectrum(M, N, scales, i, smooth=smooth, vfun=vfun, max_scale=max_scale, spacing=spacing)
         acc += s * np.fft.fft2(c[i])
         den += s * s
     return np.real(np.fft.ifft2(acc / den))
@@ -470,7 +511,7 @@ def shrink(c: np.ndarray, tau, mode: str) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 
-def half_plane(rows: int, cols: int, scales: int, i: int) -> np.ndarray:
+def half_plane(rows: int, cols: int, scales: int, i: int, spacing: str = "common") -> np.ndarray:
     """Selector h_i(omega) of the one-sided shearlet of plane i (FFT order).
 
     Sec. 3.8.2 builds complex shearlets by keeping one side of each spectrum;
@@ -487,8 +528,8 @@ def half_plane(rows: int, cols: int, scales: int, i: int) -> np.ndarray:
     kappa, _, _ = plane_table(scales)[i]
     if kappa == "lowpass":
         return np.full((rows, cols), 0.5)
-    o1, o2, _, _ = grid(rows, cols, scales)
-    ch, cv, cx = cones(rows, cols, o1, o2)
+    o1, o2, _, _ = grid(rows, cols, scales, spacing=spacing)
+    ch, cv, cx = cones(rows, cols, o1, o2, spacing)
     ny_c = (cols % 2 == 0) & (o1 == -(cols // 2))
     ny_r = (rows % 2 == 0) & (o2 == -(rows // 2))
     s_h = np.where(ny_c, np.sign(np.where(ny_r, 0, o2)), np.sign(o1))
@@ -512,7 +553,7 @@ def forward_onesided(f: np.ndarray, scales: int | None = None, **opts) -> np.nda
     out = []
     for i in range(num_planes(scales)):
         psi = spectrum(M, N, scales, i, **opts)
-        w = np.sqrt(2.0) * half_plane(M, N, scales, i) if i else 1.0
+        w = np.sqrt(2.0) * half_plane(M, N, scales, i, opts.get("spacing", "common")) if i else 1.0
         out.append(np.fft.ifft2(psi * w * F))
     return np.stack(out)
 
