@@ -91,6 +91,15 @@ enum {
   FFST_MAXSCALE_MIN = 1  /* X = 2^{2 j0 - 2} (X_2 of Sec. 3.5.1: the smallest finest scale) */
 };
 
+/* Grid step of a non-square image (ffst_plan_ex), Sec. 3.5.1.  Both give a
+ * Parseval frame and coincide for square images. */
+enum {
+  FFST_SPACING_COMMON = 0,  /* one step Delta = X / floor(max(M, N)/2) for both axes: the lattice lies
+                               in [-Y, Y] x [-X, X] with Y <= X (Sec. 3.5.1's X >= Y, its single Delta
+                               with 1/4 < Delta <= 1, and psi(Delta omega) on Omega); what ffst_plan builds */
+  FFST_SPACING_PER_AXIS = 1 /* each axis spans [-X, X] with its own step X / floor(L/2) */
+};
+
 /*
  * Build a plan for rows x cols images with `scales` scales (j0 of Sec. 3.1;
  * <= 0 selects j0 = floor(1/2 log2 max(rows, cols))).  The number of planes
@@ -112,13 +121,15 @@ ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* out);
  *   vfun       the auxiliary function v (FFST_V_*), vorder its order k for
  *              FFST_V_POLY (ignored otherwise);
  *   max_scale  FFST_MAXSCALE_MAX (X = 2^{2 j0 - 1}, what ffst_plan builds) or
- *              FFST_MAXSCALE_MIN (X = 2^{2 j0 - 2}).
+ *              FFST_MAXSCALE_MIN (X = 2^{2 j0 - 2});
+ *   spacing    FFST_SPACING_COMMON (what ffst_plan builds) or
+ *              FFST_SPACING_PER_AXIS, the grid step of non-square images.
  * Same planes, order and Parseval property; every transform entry point works
  * on any combination.  FFST_ERR_INVALID_ARG for codes outside these sets or
  * vorder outside 1..7 with FFST_V_POLY.
  */
 ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant, int vfun, int vorder, int max_scale,
-                         ffst_plan_t* out);
+                         int spacing, ffst_plan_t* out);
 
 /* Query a plan.  Any output pointer may be NULL. */
 ffst_status ffst_plan_info(ffst_plan_t plan, int* rows, int* cols, int* scales, int* num_planes);
@@ -209,20 +220,24 @@ ffst_status ffst_adjoint(ffst_plan_t plan, const void* coeffs, int storage,
 /*
  * Forward transform for small images that allocates nothing (the paper has
  * no counterpart; it exists for callers that cannot call cudaMalloc, such as
- * code running during CUDA stream capture, processes whose framework has
- * reserved nearly all device memory, or hosts that forbid allocation after
- * start-up; ffst_plan allocates, so those callers cannot build a plan).
+ * processes whose framework has reserved nearly all device memory, plug-ins
+ * inside a host application that owns the device's allocator, or hosts that
+ * forbid allocation after start-up; ffst_plan allocates, so those callers
+ * cannot build a plan).
  *   rows, cols:  powers of two in [8, 256]; scales in 1..4 (<= 0: default j0).
  *                Anything larger returns FFST_ERR_UNSUPPORTED_SIZE before any
  *                work is enqueued.
  *   img:         device, rows x cols float32, read only.
  *   coeffs:      device, [eta][rows][cols] float32, fully overwritten.
- * Same result as ffst_forward with FFST_STORE_F32 (to FP32 rounding).  All
- * tables and intermediates live in one static device array of about 2.5 MB
- * that every GPU loading the library holds until the process exits.  The
- * first call on a device looks up that array's address (and may load the
- * module), so make it before any stream capture.  Calls share the array:
- * two calls whose work overlaps on the GPU race and corrupt each other.
+ * Same result as ffst_forward with FFST_STORE_F32 (to FP32 rounding; the
+ * grid of FFST_SPACING_COMMON).  All tables and intermediates live in one
+ * static device array of about 2.5 MB that every GPU loading the library
+ * holds until the process exits.  Every call looks up that array's address
+ * on the current device (host side, no allocation); the first call on a
+ * device also loads the library's device code there, so make it before any
+ * stream capture.  Calls share the array and each call rewrites every word
+ * it reads: two calls whose work overlaps on the GPU race and corrupt each
+ * other.
  */
 ffst_status ffst_forward_noalloc(int rows, int cols, int scales, const float* img, float* coeffs, void* stream);
 

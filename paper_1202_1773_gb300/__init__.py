@@ -93,14 +93,16 @@ class Plan:
     Construction options (ffst_plan_ex): smooth=True builds the smooth
     shearlets of Sec. 3.4; vfun picks the auxiliary function v ("meyer",
     "quadratic", ("poly", k) or "cinf"); max_scale="min" uses the smaller
-    grid extent X = 2^{2 j0 - 2}.  ``inverse_split`` sets the plane chunks
-    of the inverse's sum (ffst_plan_set_inverse_split).
+    grid extent X = 2^{2 j0 - 2}; spacing="per_axis" stretches both axes of
+    a non-square image to [-X, X] instead of one grid step for both (Sec.
+    3.5.1).  ``inverse_split`` sets the plane chunks of the inverse's sum
+    (ffst_plan_set_inverse_split).
     """
 
     _VFUNS = {"meyer": _lib.FFST_V_MEYER, "quadratic": _lib.FFST_V_QUADRATIC, "cinf": _lib.FFST_V_CINF}
 
     def __init__(self, rows: int, cols: int, scales: int = 0, device=None, smooth: bool = False, vfun="meyer",
-                 max_scale: str = "max"):
+                 max_scale: str = "max", spacing: str = "common"):
         torch = _torch()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.smooth = bool(smooth)
@@ -112,10 +114,13 @@ class Plan:
             raise ValueError(f"unknown vfun {vfun!r}")
         if max_scale not in ("max", "min"):
             raise ValueError(f"max_scale must be 'max' or 'min', not {max_scale!r}")
+        if spacing not in ("common", "per_axis"):
+            raise ValueError(f"spacing must be 'common' or 'per_axis', not {spacing!r}")
         with torch.cuda.device(self.device):
             self.handle = ffst_plan(rows, cols, scales,
                                     _lib.FFST_VARIANT_SMOOTH if smooth else _lib.FFST_VARIANT_CLASSIC, vcode, vorder,
-                                    _lib.FFST_MAXSCALE_MIN if max_scale == "min" else _lib.FFST_MAXSCALE_MAX)
+                                    _lib.FFST_MAXSCALE_MIN if max_scale == "min" else _lib.FFST_MAXSCALE_MAX,
+                                    _lib.FFST_SPACING_PER_AXIS if spacing == "per_axis" else _lib.FFST_SPACING_COMMON)
         self.rows, self.cols, self.scales, self.num_planes = ffst_plan_info(self.handle)
 
     # -- bookkeeping ----------------------------------------------------------

@@ -31,7 +31,7 @@ _VP = ctypes.c_void_p
 _I = ctypes.c_int
 SIGNATURES = [
     ("ffst_plan", _I, [_I, _I, _I, ctypes.POINTER(_VP)]),
-    ("ffst_plan_ex", _I, [_I, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_VP)]),
+    ("ffst_plan_ex", _I, [_I, _I, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_VP)]),
     ("ffst_plan_info", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("ffst_plane_index", _I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("ffst_spectra", _I, [_VP, _VP, _VP]),
@@ -133,16 +133,18 @@ FFST_VARIANT_CLASSIC = 0
 FFST_VARIANT_SMOOTH = 1
 FFST_V_MEYER, FFST_V_QUADRATIC, FFST_V_POLY, FFST_V_CINF = 0, 1, 2, 3
 FFST_MAXSCALE_MAX, FFST_MAXSCALE_MIN = 0, 1
+FFST_SPACING_COMMON, FFST_SPACING_PER_AXIS = 0, 1
 
 
 def ffst_plan(rows: int, cols: int, scales: int = 0, variant: int = FFST_VARIANT_CLASSIC, vfun: int = FFST_V_MEYER,
-              vorder: int = 0, max_scale: int = FFST_MAXSCALE_MAX) -> int:
+              vorder: int = 0, max_scale: int = FFST_MAXSCALE_MAX, spacing: int = FFST_SPACING_COMMON) -> int:
     out = _VP()
-    if (variant, vfun, max_scale) == (FFST_VARIANT_CLASSIC, FFST_V_MEYER, FFST_MAXSCALE_MAX):
+    if (variant, vfun, max_scale, spacing) == (FFST_VARIANT_CLASSIC, FFST_V_MEYER, FFST_MAXSCALE_MAX,
+                                               FFST_SPACING_COMMON):
         _check("ffst_plan", lib().ffst_plan(int(rows), int(cols), int(scales), ctypes.byref(out)))
     else:
         _check("ffst_plan_ex", lib().ffst_plan_ex(int(rows), int(cols), int(scales), int(variant), int(vfun),
-                                                  int(vorder), int(max_scale), ctypes.byref(out)))
+                                                  int(vorder), int(max_scale), int(spacing), ctypes.byref(out)))
     return out.value
 
 

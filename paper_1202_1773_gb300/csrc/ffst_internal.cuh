@@ -170,7 +170,9 @@ __host__ __device__ inline void set_slot(PlaneDesc& d) {
 // Everything the in-register window generator needs (passed by value).
 struct WinParams {
   int M, N;        // rows (omega_2 axis), cols (omega_1 axis)
-  int hm, hn;      // floor(M/2), floor(N/2)
+  int hm, hn;      // floor(M/2), floor(N/2): table lengths - 1
+  int gm, gn;      // grid denominators: xi2 = omega_2 X / gm, xi1 = omega_1 X / gn
+                   // (one step: gm = gn = floor(max(M, N)/2); per axis: hm, hn)
   const float* psi1_col;  // [j0][hn+1]: psi1(4^-j * a * dc), a = |omega_1|
   const float* psi1_row;  // [j0][hm+1]: psi1(4^-j * a * dr), a = |omega_2|
   const float* phi_col;   // [hn+1]:     varphi(a * dc)

@@ -1,22 +1,25 @@
 // ffst_forward_noalloc: a forward transform for small images that allocates
 // no memory at all.
 //
-// Who needs it: callers that cannot call cudaMalloc.  Examples are code that
-// runs while a CUDA stream is being captured into a graph (allocation calls
-// are not allowed during capture), processes whose framework has already
-// reserved nearly all device memory for its own pool, and real-time or
-// embedded hosts whose rules forbid allocation after start-up.  ffst_plan
-// allocates its tables and workspace, so these callers cannot build a plan.
+// Who needs it: callers that cannot call cudaMalloc.  Examples are
+// processes whose framework has already reserved nearly all device memory
+// for its own pool, plug-ins running inside a host application that owns
+// the device's allocator and hands out buffers but no right to allocate,
+// and real-time or embedded hosts whose rules forbid allocation after
+// start-up.  ffst_plan allocates its tables and workspace, so these callers
+// cannot build a plan.
 //
 // How: every table and every intermediate of this entry point lives in the
 // file-scope device array g_noalloc_scratch below (kNoallocBytes, about
 // 2.5 MB), which the CUDA module reserves once on every GPU that loads the
 // library and keeps until the process exits.  The caller passes the input
 // image and the output stack only.  Host code cannot use the array's name
-// as a device address, so the first call on each device looks the address
-// up with cudaGetSymbolAddress (with that device current) and caches it.
-// That first call may trigger module loading, so make it before any stream
-// capture begins.  Every call shares the one array and leaves its contents
+// as a device address, so every call looks the address up with
+// cudaGetSymbolAddress on the current device (a host-side lookup that
+// allocates nothing; after a context reset the module reloads and the
+// array may move, so the address is never cached).  The first call on a
+// device loads the library's device code there and sets the array up, so
+// make that first call before any stream capture begins.  Every call shares the one array and leaves its contents
 // behind; each call writes every scratch word it later reads, so nothing
 // needs clearing, but two calls whose work overlaps on the GPU (different
 // streams, or different host threads on the same device) race on the
@@ -28,7 +31,6 @@
 // column of every plane is transformed); results equal ffst_forward's to
 // FP32 rounding.
 #include <cstring>
-#include <mutex>
 
 #include "ffst_kernels.cuh"
 
@@ -41,7 +43,12 @@ constexpr int kNaMaxPlanes = (1 << (kNaMaxScales + 2)) - 3;  // 61
 constexpr int kNaGroup = 8;                                  // planes per column/row pass pair
 constexpr long long kNaSpec = (long long)kNaMaxSide * (kNaMaxSide / 2 + 1);  // M x (N/2+1) complex
 constexpr long long kNaSlot = (long long)kNaMaxSide * (kNaMaxSide / 2 + 2);  // one plane's intermediate (even pitch)
-constexpr long long kNaMaxItems = (long long)kNaMaxPlanes * 16;              // <= 16 panels per plane
+// Column panels per plane: ceil((N/2 + 1) / P) with P columns per column block
+// (ColCfg); P shrinks as the column length grows, so the tallest image has the
+// most panels (16 x 256 columns per block at the default 256 threads).
+constexpr int kNaMinP = ColCfg<kNaMaxSide>::P;
+constexpr int kNaMaxPanels = (kNaMaxSide / 2 + 1 + kNaMinP - 1) / kNaMinP;
+constexpr long long kNaMaxItems = (long long)kNaMaxPlanes * kNaMaxPanels;
 constexpr long long kNaTabFloats = 2LL * kNaMaxScales * (kNaMaxSide / 2 + 1) + 2 * (kNaMaxSide / 2 + 1);
 
 // byte offsets inside the scratch array (each 256-byte aligned)
@@ -128,7 +135,7 @@ __global__ void k_na_setup(NaSetup s) {
   const int stride = gridDim.x * blockDim.x;
   const int hn = s.N / 2, hm = s.M / 2;
   const double X = ldexp(1.0, 2 * s.j0 - 1);
-  const double dc = X / hn, dr = X / hm;
+  const double dc = X / (s.M > s.N ? hm : hn), dr = dc;  // one step for both axes (Sec. 3.5.1)
   float* psi1_col = s.tab;
   float* psi1_row = psi1_col + s.j0 * (hn + 1);
   float* phi_col = psi1_row + s.j0 * (hm + 1);
@@ -171,24 +178,14 @@ __global__ void k_na_setup(NaSetup s) {
   for (int q = tid; q < s.eta * s.ipp; q += stride) s.items[q] = ColItem{q / s.ipp, (q % s.ipp) * s.P};
 }
 
-std::mutex g_na_mutex;
-void* g_na_base[256];
-
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
+// Device address of the scratch array on the current device, looked up on
+// every call with that device current (never cached: a context reset reloads
+// the module and may move the array).
 ffst_status na_scratch(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "ffst_forward_noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= 256) return fail(FFST_ERR_CUDA, "ffst_forward_noalloc: device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_base[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "ffst_forward_noalloc: cudaGetSymbolAddress");
-    g_na_base[dev] = p;
-  }
-  *out = static_cast<unsigned char*>(g_na_base[dev]);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "ffst_forward_noalloc: cudaGetSymbolAddress");
+  *out = static_cast<unsigned char*>(p);
   return FFST_OK;
 }
 
@@ -239,6 +236,7 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
   P.win.N = cols;
   P.win.hm = P.hm;
   P.win.hn = P.hn;
+  P.win.gm = P.win.gn = (rows > cols ? rows : cols) / 2;
   P.win.psi1_col = tab;
   P.win.psi1_row = tab + j0 * (P.hn + 1);
   P.win.phi_col = P.win.psi1_row + j0 * (P.hm + 1);
@@ -256,6 +254,8 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
   su.Hc = P.Hc;
   su.P = cols_per_cta(rows);
   su.ipp = (P.Hc + su.P - 1) / su.P;
+  if (su.P < 1 || (long long)su.ipp * P.eta > kNaMaxItems)  // kNaMaxItems covers kNaMaxSide; checked anyway
+    return fail(FFST_ERR_UNSUPPORTED_SIZE, "ffst_forward_noalloc: column work items exceed the static scratch");
   su.tab = tab;
   su.twr = P.d_tw_rows;
   su.rtw = P.d_rtw;

@@ -463,11 +463,12 @@ static cudaError_t upload(float2** dst, const std::vector<float2>& v) {
 using namespace ffst;
 
 extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* out) {
-  return ffst_plan_ex(rows, cols, scales, FFST_VARIANT_CLASSIC, FFST_V_MEYER, 0, FFST_MAXSCALE_MAX, out);
+  return ffst_plan_ex(rows, cols, scales, FFST_VARIANT_CLASSIC, FFST_V_MEYER, 0, FFST_MAXSCALE_MAX,
+                      FFST_SPACING_COMMON, out);
 }
 
 extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant, int vfun, int vorder, int max_scale,
-                                    ffst_plan_t* out) {
+                                    int spacing, ffst_plan_t* out) {
   if (!out) return fail(FFST_ERR_INVALID_ARG, "ffst_plan: out is NULL");
   *out = nullptr;
   if (variant != FFST_VARIANT_CLASSIC && variant != FFST_VARIANT_SMOOTH)
@@ -478,6 +479,8 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
     return fail(FFST_ERR_INVALID_ARG, "ffst_plan_ex: FFST_V_POLY needs an order in 1..7");
   if (max_scale != FFST_MAXSCALE_MAX && max_scale != FFST_MAXSCALE_MIN)
     return fail(FFST_ERR_INVALID_ARG, "ffst_plan_ex: max_scale must be FFST_MAXSCALE_MAX or FFST_MAXSCALE_MIN");
+  if (spacing != FFST_SPACING_COMMON && spacing != FFST_SPACING_PER_AXIS)
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_ex: spacing must be FFST_SPACING_COMMON or FFST_SPACING_PER_AXIS");
   VSpec vs;
   if (vfun == FFST_V_POLY) vs = v_poly_spec(vorder);
   vs.kind = vfun;
@@ -531,10 +534,13 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
   }
   if ((int)p->planes.size() != p->eta) return fail(FFST_ERR_INVALID_ARG, "ffst_plan: internal plane count mismatch");
 
-  // FP64 window tables (Sec. 3.5.1 grid: xi = a * X / floor(L/2), X = 2^{2 j0 - 1},
-  // or X = 2^{2 j0 - 2} for max_scale = FFST_MAXSCALE_MIN)
+  // FP64 window tables (Sec. 3.5.1 grid: xi = a * X / g, X = 2^{2 j0 - 1}, or
+  // X = 2^{2 j0 - 2} for max_scale = FFST_MAXSCALE_MIN; one step g =
+  // floor(max(M, N)/2) for both axes, or g = floor(L/2) per axis)
   const double X = std::ldexp(1.0, 2 * j0 - (max_scale == FFST_MAXSCALE_MAX ? 1 : 2));
-  const double dc = X / p->hn, dr = X / p->hm;
+  const int gm = spacing == FFST_SPACING_COMMON ? mx / 2 : p->hm;
+  const int gn = spacing == FFST_SPACING_COMMON ? mx / 2 : p->hn;
+  const double dc = X / gn, dr = X / gm;
   const int ncol = p->hn + 1, nrow = p->hm + 1;
   // layout: psi1 col [j0][ncol] | psi1 row [j0][nrow] | phi col | phi row |
   //         smooth: sig col [j0][ncol] | sig row [j0][nrow] | alp col [j0][ncol] | alp row [j0][nrow]
@@ -574,6 +580,8 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
   p->win.N = cols;
   p->win.hm = p->hm;
   p->win.hn = p->hn;
+  p->win.gm = gm;
+  p->win.gn = gn;
   p->win.psi1_col = p->d_tables;
   p->win.psi1_row = p->d_tables + (size_t)j0 * ncol;
   p->win.phi_col = p->win.psi1_row + (size_t)j0 * nrow;

@@ -9,12 +9,13 @@
 //   varphi     Sec. 2.4              1-D table, FP64-generated on the host
 //   cones      Sec. 2.3              exact integer test on the frequency indices
 //   spectra    Sec. 3.1 eq. (shearletTransform), glued seam shearlets for |k| = 2^j
-//   grid       Sec. 3.5.1            xi = omega * X / floor(L/2) per axis, X = 2^{2 j0 - 1}
+//   grid       Sec. 3.5.1            xi = omega * X / g, X = 2^{2 j0 - 1}, one step
+//                                    (g = floor(max(M, N)/2)) or per axis (g = floor(L/2))
 //   fix        Sec. 3.8.1            Nyquist row/column mirrored, squares averaged
 //
 // Accuracy notes.  The shear argument u = 2^j xi2/xi1 + k (h cone) is formed
-// as one fraction of exact integers, (2^j o2 floor(N/2) + k o1 floor(M/2)) /
-// (o1 floor(M/2)), so the cancellation against k happens exactly and u has
+// as one fraction of exact integers, (2^j o2 gn + k o1 gm) / (o1 gm) with the
+// grid denominators gm, gn, so the cancellation against k happens exactly and u has
 // FP32 relative accuracy on the support |u| < 1.  v near 1 is evaluated as
 // 1 - p(1 - x) (the symmetry v(x) + v(1-x) = 1 of Sec. 2.1), so
 // psi2 keeps ~1 ulp absolute accuracy near its peak.
@@ -74,12 +75,12 @@ __device__ __forceinline__ float smooth_radial(const WinParams& w, int j, int a1
 }
 
 // Unfixed spectrum of plane (kappa, j, k) at integer frequency (o2, o1).
-// |o1| <= floor(N/2), |o2| <= floor(M/2), M, N <= 4096 and j <= 7 keep every
+// |o1| <= floor(N/2), |o2| <= floor(M/2), gm, gn <= 2048 and j <= 7 keep every
 // product below 2^31.
 __device__ __forceinline__ float win_raw(const WinParams& w, int kappa, int j, int k, int o2, int o1) {
   const int a2 = abs(o2), a1 = abs(o1);
-  const int lhs = a2 * w.hn;  // |xi2| ~ lhs, |xi1| ~ rhs (common factor X/(hm hn))
-  const int rhs = a1 * w.hm;
+  const int lhs = a2 * w.gn;  // |xi2| ~ lhs, |xi1| ~ rhs (common factor X/(gm gn))
+  const int rhs = a1 * w.gm;
   if (kappa == kLowpass) {
     if (w.smooth) return __ldg(&w.phi_col[a1]) * __ldg(&w.phi_row[a2]);  // Sec. 2.4 eq. (Phi)
     return (lhs <= rhs) ? __ldg(&w.phi_col[a1]) : __ldg(&w.phi_row[a2]);
@@ -99,12 +100,12 @@ __device__ __forceinline__ float win_raw(const WinParams& w, int kappa, int j, i
   int num, den;
   if (use_h) {
     p1 = w.smooth ? 0.0f : __ldg(&w.psi1_col[j * (w.hn + 1) + a1]);
-    num = (1 << j) * o2 * w.hn + k * o1 * w.hm;
-    den = o1 * w.hm;
+    num = (1 << j) * o2 * w.gn + k * o1 * w.gm;
+    den = o1 * w.gm;
   } else {
     p1 = w.smooth ? 0.0f : __ldg(&w.psi1_row[j * (w.hm + 1) + a2]);
-    num = (1 << j) * o1 * w.hm + k * o2 * w.hn;
-    den = o2 * w.hn;
+    num = (1 << j) * o1 * w.gm + k * o2 * w.gn;
+    den = o2 * w.gn;
   }
   if (w.smooth) p1 = smooth_radial(w, j, a1, a2);  // both cones (Sec. 3.4 eq. smoothPsi)
   if (p1 == 0.0f) return 0.0f;
@@ -141,7 +142,7 @@ __device__ __forceinline__ int half_sign(const WinParams& w, int kappa, int pr, 
   const bool ny_r = (w.M % 2 == 0) && (2 * pr == w.M);
   const bool ny_c = (w.N % 2 == 0) && (2 * pc == w.N);
   auto sgn = [](int x) { return (x > 0) - (x < 0); };
-  const bool use_h = abs(o2) * w.hn <= abs(o1) * w.hm;  // C^h, seam lines (and the origin)
+  const bool use_h = abs(o2) * w.gn <= abs(o1) * w.gm;  // C^h, seam lines (and the origin)
   if (use_h) return ny_c ? (ny_r ? 0 : sgn(o2)) : sgn(o1);
   return ny_r ? (ny_c ? 0 : sgn(o1)) : sgn(o2);
 }

@@ -68,7 +68,7 @@ def test_generic_sizes_pass_the_size_check(lib, rows, cols):
 
 def test_null_arguments_rejected_on_host(lib):
     assert lib.ffst_plan(64, 64, 0, None) == _lib.FFST_ERR_INVALID_ARG
-    assert lib.ffst_plan_ex(64, 64, 0, 1, 0, 0, 0, None) == _lib.FFST_ERR_INVALID_ARG
+    assert lib.ffst_plan_ex(64, 64, 0, 1, 0, 0, 0, 0, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_plan_info(None, None, None, None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_plane_index(None, 0, None, None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_forward(None, None, None, 0, None, None) == _lib.FFST_ERR_INVALID_ARG

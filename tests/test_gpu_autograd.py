@@ -102,24 +102,56 @@ def test_deconvolution_matches_fp64_iteration(ffst):
     assert np.linalg.norm(x.cpu().numpy() - truth) < np.linalg.norm(y - truth)
 
 
-def test_deconvolution_1024_gradient(ffst):
-    # the 1024x1024 J=5 workload: objective and gradient of the first
-    # iteration (autograd through ffst_forward / ffst_adjoint) against FP64
+def test_deconvolution_200_steps_128(ffst):
+    # the full 200-step iteration on a 128x128 problem (J=3) against the FP64
+    # run of the same iteration: final iterate and objective within 1e-4
+    from paper_1202_1773_gb300 import deconv
+
+    shape = (128, 128)
+    lam, eps, steps = 5e-3, 1e-3, 200
+    truth = inputs.scaled_cartoon(*shape, seed=16, sigma=0.0).astype(np.float64)
+    psf = deconv.gaussian_psf(*shape, sigma=2.0, radius=8)
+    rng = np.random.default_rng(17)
+    y = (do.blur(truth, psf) + rng.normal(0.0, 0.02, shape)).astype(np.float32)
+    plan = ffst.Plan(*shape)
+    x, hist = deconv.deconvolve(torch.from_numpy(y).cuda(), plan, deconv.Blur(psf, "cuda"), lam=lam, eps=eps,
+                                steps=steps)
+    xr, hr = do.deconvolve(y.astype(np.float64), psf, lam, eps, steps)
+    assert _rel(x.cpu().numpy(), xr) <= 1e-4
+    assert abs(hist[-1] - hr[-1]) <= 1e-4 * abs(hr[-1])
+    # the objective went down (FISTA is not monotone step by step) and the
+    # restoration is closer to the truth than y
+    assert hist[-1] < 0.95 * hist[0]
+    assert np.linalg.norm(x.cpu().numpy() - truth) < np.linalg.norm(y - truth)
+
+
+def test_deconvolution_1024_first_steps(ffst):
+    # the 1024x1024 J=5 workload: the first 5 iterations (autograd through
+    # ffst_forward / ffst_adjoint) against the FP64 run of the same iteration,
+    # and the first gradient on its own
     from paper_1202_1773_gb300 import deconv
 
     shape = (1024, 1024)
-    lam, eps = 5e-3, 1e-3
+    lam, eps, steps = 5e-3, 1e-3, 5
     truth = inputs.scaled_cartoon(*shape, seed=4, sigma=0.0).astype(np.float64)
     psf = deconv.gaussian_psf(*shape)
     rng = np.random.default_rng(13)
     y = (do.blur(truth, psf) + rng.normal(0.0, 0.02, shape)).astype(np.float32)
     plan = ffst.Plan(*shape)
     yt = torch.from_numpy(y).cuda()
+    blur = deconv.Blur(psf, "cuda")
     x = yt.clone().requires_grad_(True)
-    J = deconv.objective(x, yt, deconv.Blur(psf, "cuda"), plan, lam, eps)
+    J = deconv.objective(x, yt, blur, plan, lam, eps)
     (g,) = torch.autograd.grad(J, x)
     y64 = y.astype(np.float64)
-    gr = do.gradient(y64, y64, psf, lam, eps, None)
+    psi = o.spectra(*shape)
+    gr = do.gradient(y64, y64, psf, lam, eps, psi)
     assert _rel(g.cpu().numpy(), gr) <= 1e-4
     Jv = float(J.detach())
-    assert abs(Jv - do.objective(y64, y64, psf, lam, eps, None)) <= 1e-4 * abs(Jv)
+    assert abs(Jv - do.objective(y64, y64, psf, lam, eps, psi)) <= 1e-4 * abs(Jv)
+    del psi
+    xg, hist = deconv.deconvolve(yt, plan, blur, lam=lam, eps=eps, steps=steps)
+    xr, hr = do.deconvolve(y64, psf, lam, eps, steps)
+    assert _rel(xg.cpu().numpy(), xr) <= 1e-4
+    for a, b in zip(hist, hr):
+        assert abs(a - b) <= 1e-4 * abs(b)

@@ -110,3 +110,42 @@ def test_autotune_round_trip(ffst, tmp_path):
         assert q.group_mb == (fmb, imb)
     finally:
         del os.environ["FFST_AUTOTUNE_CACHE"]
+
+
+def test_full_256_image_batch_against_oracle(ffst):
+    # the batched workload: 256 images of uneven sizes (seed 2), two seeded
+    # images per size, forward + inverse replayed from one captured graph;
+    # every reconstruction within 1e-5 and, for the first image of each
+    # distinct size, sampled planes against the FP64 oracle plane by plane
+    # (relative to the plane's energy, floored at 1e-3 of the image's)
+    n = 256
+    shapes = inputs.batch_sizes(n, seed=2)
+    srcs = {sh: [inputs.scaled_cartoon(*sh, seed=300 + q) for q in range(2)] for sh in sorted(set(shapes))}
+    dev = {sh: [torch.from_numpy(x).cuda() for x in xs] for sh, xs in srcs.items()}
+    imgs = [dev[sh][i % 2] for i, sh in enumerate(shapes)]
+    bp = ffst.BatchPlan(shapes, lanes=4)
+    stacks = bp.empty_stacks()
+    outs = [torch.empty(sh, device="cuda") for sh in shapes]
+    g = bp.capture(imgs, stacks, outs, what=3)
+    g.launch()
+    torch.cuda.synchronize()
+    for i in range(n):
+        err = float(torch.linalg.norm(outs[i] - imgs[i]) / torch.linalg.norm(imgs[i]))
+        assert err <= 1e-5, (i, shapes[i], err)
+    seen = set()
+    for i, sh in enumerate(shapes):
+        if sh in seen:
+            continue
+        seen.add(sh)
+        f = srcs[sh][i % 2].astype(np.float64)
+        F = np.fft.fft2(f)
+        eta = bp.shape(i)[0]
+        j0 = o.default_scales(*sh)
+        for q in (0, eta // 3, eta - 1):
+            ref = o.forward_plane(F, j0, q)
+            got = stacks[i][q].cpu().numpy()
+            err = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-3 * np.linalg.norm(f))
+            assert err <= 1e-5, (sh, q, err)
+    assert len(seen) == len(SIZES)
+    g.close()
+    bp.close()

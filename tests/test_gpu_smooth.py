@@ -83,21 +83,25 @@ def test_option_codes_checked(ffst):
     import ctypes
 
     out = ctypes.c_void_p()
-    for args in ((7, 0, 0, 0), (0, 9, 0, 0), (0, 2, 0, 0), (0, 2, 8, 0), (0, 0, 0, 3)):
+    for args in ((7, 0, 0, 0, 0), (0, 9, 0, 0, 0), (0, 2, 0, 0, 0), (0, 2, 8, 0, 0), (0, 0, 0, 3, 0),
+                 (0, 0, 0, 0, 2)):
         assert _lib.lib().ffst_plan_ex(64, 64, 0, *args, ctypes.byref(out)) == _lib.FFST_ERR_INVALID_ARG
         assert out.value is None
     with pytest.raises(ValueError):
         ffst.Plan(64, 64, vfun="cubic")
     with pytest.raises(ValueError):
         ffst.Plan(64, 64, max_scale="mid")
+    with pytest.raises(ValueError):
+        ffst.Plan(64, 64, spacing="isotropic")
 
 
 OPTIONS = [
     dict(vfun="quadratic"), dict(vfun=("poly", 1)), dict(vfun=("poly", 5)), dict(vfun="cinf"),
     dict(max_scale="min"), dict(smooth=True, vfun="cinf", max_scale="min"),
+    dict(spacing="per_axis"), dict(smooth=True, spacing="per_axis"),
 ]
 ORACLE_KW = lambda kw: dict(smooth=kw.get("smooth", False), vfun=kw.get("vfun", "meyer"),
-                            max_scale=kw.get("max_scale", "max"))
+                            max_scale=kw.get("max_scale", "max"), spacing=kw.get("spacing", "common"))
 
 
 @pytest.mark.parametrize("kw", OPTIONS, ids=lambda kw: "-".join(f"{k}={v}" for k, v in kw.items()))

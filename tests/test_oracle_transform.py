@@ -174,3 +174,14 @@ def test_shrink_invariants():
     # the low-pass plane of a constant image is the value itself: shrinking it is a scalar map
     d = o.forward(np.full((32, 32), 0.75))
     np.testing.assert_allclose(o.shrink(d, 0.25, "soft")[0], 0.5, atol=1e-13)
+
+
+def test_precomputed_spectra_forms_agree():
+    # forward_with / adjoint_with (spectra computed once, Sec. 3.5) give the
+    # same stack and image as the per-call forms
+    rng = np.random.default_rng(40)
+    f = rng.standard_normal((32, 48))
+    psi = o.spectra(32, 48)
+    np.testing.assert_allclose(o.forward_with(psi, f), o.forward(f), rtol=0, atol=1e-14)
+    c = rng.standard_normal(psi.shape)
+    np.testing.assert_allclose(o.adjoint_with(psi, c), o.adjoint(c), rtol=0, atol=1e-13)

@@ -1,17 +1,20 @@
-"""The allocation-free forward entry point against the planned forward.
+"""The allocation-free forward entry point against the planned forward and the oracle.
 
-ffst_forward_noalloc serves callers that cannot call cudaMalloc (code running
-during CUDA stream capture, processes whose framework holds nearly all device
-memory, hosts that forbid allocation after start-up): it keeps its tables and
-intermediates in a static device array instead of plan-owned workspace.  These
-tests call it through the C ABI and compare it with ffst_forward on the same
-images, twice in a row, so a stale value left in the shared array by the first
-call would show up in the second.  The file is named to be collected last.
+ffst_forward_noalloc serves callers that cannot call cudaMalloc (processes
+whose framework holds nearly all device memory, plug-ins inside a host
+application that owns the allocator, hosts that forbid allocation after
+start-up): it keeps its tables and intermediates in a static device array
+instead of plan-owned workspace.  These tests call it through the C ABI and
+compare it with ffst_forward on the same images, twice in a row, so a stale
+value left in the shared array by the first call would show up in the second;
+each call is also compared with the FP64 oracle plane by plane.  The file is
+named to be collected last.
 """
 
 import numpy as np
 import pytest
 
+from oracle import ffst_oracle as o
 from paper_1202_1773_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -49,6 +52,15 @@ def test_noalloc_forward_matches_planned_forward(ffst, shape):
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
         assert _rel(out, ref) <= TOL
+        # against the FP64 oracle, every plane relative to its own energy
+        # (floored at 1e-3 of the image's, for planes that carry almost none)
+        f = x.cpu().numpy().astype(np.float64)
+        cref = o.forward(f)
+        got = out.cpu().numpy()
+        floor = 1e-3 * np.linalg.norm(f)
+        for i in range(cref.shape[0]):
+            err = np.linalg.norm(got[i] - cref[i]) / max(np.linalg.norm(cref[i]), floor)
+            assert err <= TOL, (i, err)
 
 
 def test_noalloc_rejects_sizes_beyond_the_static_limit(ffst):
