@@ -482,6 +482,23 @@ def inverse(c: np.ndarray, scales: int | None = None, smooth: bool = False, vfun
     return np.real(np.fft.ifft2(acc / den))
 
 
+def forward_with(psi: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """Real coefficient stack from precomputed spectra psi = spectra(M, N, ...):
+    c_i = Re ifft2(psi_i * fft2(f)), Sec. 3.1 eq. (shearletTransform).  Sec. 3.5
+    precomputes the spectra once and uses them for both directions; this is
+    that form, for loops that transform many images of one size."""
+    F = np.fft.fft2(np.asarray(f, dtype=np.float64))
+    return np.stack([np.real(np.fft.ifft2(psi[i] * F)) for i in range(psi.shape[0])])
+
+
+def adjoint_with(psi: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """T* c = Re ifft2(sum_i psi_i * fft2(c_i)) from precomputed spectra (Sec. 3.3)."""
+    acc = np.zeros(psi.shape[1:], dtype=np.complex128)
+    for i in range(psi.shape[0]):
+        acc += psi[i] * np.fft.fft2(np.asarray(c[i], dtype=np.float64))
+    return np.real(np.fft.ifft2(acc))
+
+
 def mean_abs(c: np.ndarray) -> np.ndarray:
     """d(i) = 1/(MN) sum |c(., ., i)|, Sec. 3.5.2 eq. (shearlet_meanvalue)."""
     c = np.asarray(c)
