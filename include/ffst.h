@@ -300,6 +300,45 @@ ffst_status ffst_plan_get_schedule(ffst_plan_t plan, int* mode);
  * bytes).  FFST_ERR_INVALID_ARG for nsplit outside 0..16.
  */
 ffst_status ffst_plan_set_inverse_split(ffst_plan_t plan, int nsplit);
+
+/*
+ * Plane-sharded transforms.  The planes of Sec. 3.1 are independent: a
+ * forward over a plane range needs only fft2(f), and the inverse of Sec. 3.3
+ * is a sum over planes, so ranks holding disjoint ranges combine their
+ * partial spectra with one sum-reduce and one rank finishes.
+ *
+ * ffst_plan_set_planes restricts the plan's plane passes to [p0, p1)
+ * (0 <= p0 < p1 <= eta; the default is every plane).  Afterwards
+ * ffst_forward, ffst_forward_stats and ffst_forward_complex write only those
+ * planes: `coeffs` holds p1 - p0 planes (plane p0 first); plane_scale and
+ * the statistics keep eta entries indexed by the global plane (entries
+ * outside the range are unspecified).  ffst_inverse, ffst_adjoint and
+ * ffst_inverse_partial read a stack of p1 - p0 planes.  Regroups the plan
+ * (synchronises the device; allocates).  FFST_ERR_INVALID_ARG for an empty
+ * or out-of-range interval, or while the persistent schedule is selected.
+ */
+ffst_status ffst_plan_set_planes(ffst_plan_t plan, int p0, int p1);
+ffst_status ffst_plan_get_planes(ffst_plan_t plan, int* p0, int* p1);
+
+/*
+ * Partial inverse: spectrum = sum over the active planes i of
+ * psi_hat_i * fft2(c_i), the half spectrum [rows][cols/2+1] of complex64
+ * (interleaved re, im; device, caller-owned, fully overwritten), summed in
+ * the plan's fixed plane order.  Sec. 3.3 eq. (inverseShearletTransform)
+ * before its ifft2; the sum of the partial spectra of disjoint ranges that
+ * cover every plane is the full sum.
+ */
+ffst_status ffst_inverse_partial(ffst_plan_t plan, const void* coeffs, int storage, const float* plane_scale,
+                                 float* spectrum, void* stream);
+
+/*
+ * Finish an inverse from a (reduced) half spectrum as written by
+ * ffst_inverse_partial: img = ifft2(spectrum / sum_i psi_hat_i^2) over all
+ * eta planes when normalise != 0 (ffst_inverse), without the division
+ * otherwise (ffst_adjoint).  `spectrum` is used as workspace and left
+ * unspecified; img is device rows x cols float32, overwritten.
+ */
+ffst_status ffst_inverse_finish(ffst_plan_t plan, float* spectrum, int normalise, float* img, void* stream);
 ffst_status ffst_plan_get_inverse_split(ffst_plan_t plan, int* nsplit);
 
 /* Shape of the persistent schedule (zeros until it is built): resident

@@ -122,6 +122,7 @@ class Plan:
                                     _lib.FFST_MAXSCALE_MIN if max_scale == "min" else _lib.FFST_MAXSCALE_MAX,
                                     _lib.FFST_SPACING_PER_AXIS if spacing == "per_axis" else _lib.FFST_SPACING_COMMON)
         self.rows, self.cols, self.scales, self.num_planes = ffst_plan_info(self.handle)
+        self.p0, self.p1 = 0, self.num_planes
 
     # -- bookkeeping ----------------------------------------------------------
     def close(self):
@@ -145,7 +146,20 @@ class Plan:
 
     @property
     def shape(self):
+        """Shape of a coefficient stack: the active planes [p0, p1) (all by default)."""
+        return (self.p1 - self.p0, self.rows, self.cols)
+
+    @property
+    def full_shape(self):
         return (self.num_planes, self.rows, self.cols)
+
+    def set_planes(self, p0: int, p1: int):
+        """Restrict the transforms to the planes [p0, p1) (ffst_plan_set_planes):
+        stacks then hold those planes only, plane p0 first."""
+        torch = _torch()
+        with torch.cuda.device(self.device):
+            _lib.ffst_plan_set_planes(self.handle, p0, p1)
+        self.p0, self.p1 = int(p0), int(p1)
 
     def _stream(self):
         return _torch().cuda.current_stream(self.device).cuda_stream
@@ -165,10 +179,12 @@ class Plan:
 
     # -- transforms -----------------------------------------------------------
     def spectra(self, out=None):
+        """Every plane's spectrum psi_hat_i, [eta, rows, cols] in FFT order."""
         torch = _torch()
         if out is None:
-            out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
-        self._check_coeffs(out)
+            out = torch.empty(self.full_shape, dtype=torch.float32, device=self.device)
+        if out.device != self.device or tuple(out.shape) != self.full_shape or not out.is_contiguous():
+            raise ValueError(f"expected a contiguous {self.full_shape} tensor on {self.device}")
         ffst_spectra(self.handle, out, self._stream())
         return out
 
@@ -261,6 +277,36 @@ class Plan:
 
     def adjoint(self, coeffs, plane_scale=None, out=None):
         return self._synth(ffst_adjoint, coeffs, plane_scale, out)
+
+    def inverse_partial(self, coeffs, plane_scale=None, out=None):
+        """sum over the active planes of psi_hat_i * fft2(c_i): the half spectrum
+        [rows, cols//2 + 1] as complex64 (ffst_inverse_partial)."""
+        torch = _torch()
+        self._check_coeffs(coeffs)
+        storage = _storage_of(coeffs.dtype)
+        if storage != FFST_STORE_F32 and plane_scale is None:
+            raise ValueError("plane_scale is required for float16/bfloat16 coefficients")
+        shape = (self.rows, self.cols // 2 + 1)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.complex64, device=self.device)
+        if out.dtype != torch.complex64 or tuple(out.shape) != shape or not out.is_contiguous():
+            raise ValueError(f"expected a contiguous complex64 tensor of shape {shape}")
+        _lib.ffst_inverse_partial(self.handle, coeffs, storage, plane_scale if storage != FFST_STORE_F32 else None,
+                                  torch.view_as_real(out), self._stream())
+        return out
+
+    def inverse_finish(self, spectrum, normalise: bool = True, out=None):
+        """Image from a (reduced) half spectrum of inverse_partial; `spectrum` is
+        overwritten (ffst_inverse_finish)."""
+        torch = _torch()
+        shape = (self.rows, self.cols // 2 + 1)
+        if spectrum.dtype != torch.complex64 or tuple(spectrum.shape) != shape or not spectrum.is_contiguous():
+            raise ValueError(f"expected a contiguous complex64 tensor of shape {shape}")
+        if out is None:
+            out = torch.empty((self.rows, self.cols), dtype=torch.float32, device=self.device)
+        self._check_img(out)
+        _lib.ffst_inverse_finish(self.handle, torch.view_as_real(spectrum), normalise, out, self._stream())
+        return out
 
     # -- tuning ---------------------------------------------------------------
     def autotune(self, dtype=None, reps: int = 3):

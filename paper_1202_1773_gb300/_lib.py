@@ -47,6 +47,10 @@ SIGNATURES = [
     ("ffst_plan_set_schedule", _I, [_VP, _I]),
     ("ffst_plan_get_schedule", _I, [_VP, ctypes.POINTER(_I)]),
     ("ffst_plan_set_inverse_split", _I, [_VP, _I]),
+    ("ffst_plan_set_planes", _I, [_VP, _I, _I]),
+    ("ffst_plan_get_planes", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    ("ffst_inverse_partial", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
+    ("ffst_inverse_finish", _I, [_VP, _VP, _I, _VP, _VP]),
     ("ffst_plan_get_inverse_split", _I, [_VP, ctypes.POINTER(_I)]),
     ("ffst_plan_check", _I, [_VP, _VP]),
     ("ffst_plan_schedule_info", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -228,6 +232,26 @@ def ffst_plan_check(plan: int, stream: int = 0) -> int:
 
 def ffst_plan_set_inverse_split(plan: int, nsplit: int):
     _check("ffst_plan_set_inverse_split", lib().ffst_plan_set_inverse_split(plan, int(nsplit)))
+
+
+def ffst_plan_set_planes(plan: int, p0: int, p1: int):
+    _check("ffst_plan_set_planes", lib().ffst_plan_set_planes(plan, int(p0), int(p1)))
+
+
+def ffst_plan_get_planes(plan: int):
+    a, b = _I(), _I()
+    _check("ffst_plan_get_planes", lib().ffst_plan_get_planes(plan, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def ffst_inverse_partial(plan: int, coeffs, storage: int, plane_scale, spectrum, stream=None):
+    _check("ffst_inverse_partial", lib().ffst_inverse_partial(plan, _ptr(coeffs), int(storage), _ptr(plane_scale),
+                                                              _ptr(spectrum), stream))
+
+
+def ffst_inverse_finish(plan: int, spectrum, normalise: bool, img, stream=None):
+    _check("ffst_inverse_finish", lib().ffst_inverse_finish(plan, _ptr(spectrum), int(bool(normalise)), _ptr(img),
+                                                            stream))
 
 
 def ffst_plan_get_inverse_split(plan: int) -> int:

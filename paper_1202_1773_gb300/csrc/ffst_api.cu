@@ -6,6 +6,7 @@
 //   inverse:  S = 0;  rows(0);  [rows(g) | cols(g-1)] for g = 1..G-1;  cols(G-1);  ifft2(S)
 // where [a | b] is one fused launch whose blocks interleave both passes
 // (square images); other sizes run the same passes as separate launches.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 
@@ -66,7 +67,7 @@ static bool use_fused(const ffst_plan_s* p) {
 // Persistent schedule when the plan has one and its mode selects it.
 static bool use_sched(const ffst_plan_s* p) { return p->sched.on && p->sched_mode != 0; }
 
-static Group all_planes(const ffst_plan_s* p) { return Group{0, p->eta, 0, 0, p->total_items}; }
+static Group all_planes(const ffst_plan_s* p) { return Group{p->pr0, p->pr1, 0, 0, p->total_items}; }
 
 // Fused per-plane statistics and shrinkage of a forward (ffst_forward_stats).
 struct StatsOpts {
@@ -132,7 +133,8 @@ static C2RArgs plane_c2r_args(const ffst_plan_s* p, const Group& g, const float2
   a.ld = 0;
   a.M = p->M;
   a.plane0 = g.p0;
-  a.dst = static_cast<char*>(coeffs) + (long long)g.p0 * plane * (storage == FFST_STORE_F32 ? 4 : 2);
+  // the caller's stack holds the active planes [pr0, pr1)
+  a.dst = static_cast<char*>(coeffs) + (long long)(g.p0 - p->pr0) * plane * (storage == FFST_STORE_F32 ? 4 : 2);
   a.dst_plane_stride = plane;
   a.st = storage;
   a.plane_scale = plane_scale;
@@ -146,7 +148,7 @@ static C2RArgs plane_c2r_args(const ffst_plan_s* p, const Group& g, const float2
   a.cplx = 0;
   if (so && so->cplx_part >= 0) {  // planar complex stack [eta][2][M][N]: this part of each plane
     a.cplx = 1;
-    a.dst = static_cast<char*>(coeffs) + ((long long)g.p0 * 2 + so->cplx_part) * plane * sizeof(float);
+    a.dst = static_cast<char*>(coeffs) + ((long long)(g.p0 - p->pr0) * 2 + so->cplx_part) * plane * sizeof(float);
     a.dst_plane_stride = 2 * plane;
   }
   return a;
@@ -156,13 +158,13 @@ static R2CArgs plane_r2c_args(const ffst_plan_s* p, const Group& g, const void* 
                               const float* plane_scale, float2* H, bool cplx = false) {
   const long long plane = (long long)p->M * p->N;
   R2CArgs a;
-  a.src = static_cast<const char*>(coeffs) + (long long)g.p0 * plane * (storage == FFST_STORE_F32 ? 4 : 2);
+  a.src = static_cast<const char*>(coeffs) + (long long)(g.p0 - p->pr0) * plane * (storage == FFST_STORE_F32 ? 4 : 2);
   a.src_plane_stride = plane;
   a.st = storage;
   a.plane_scale = plane_scale;
   a.cplx = cplx ? 1 : 0;
   if (cplx) {  // real parts of the planar complex stack [eta][2][M][N]
-    a.src = static_cast<const char*>(coeffs) + (long long)g.p0 * 2 * plane * sizeof(float);
+    a.src = static_cast<const char*>(coeffs) + (long long)(g.p0 - p->pr0) * 2 * plane * sizeof(float);
     a.src_plane_stride = 2 * plane;
   }
   a.plane0 = g.p0;
@@ -280,8 +282,11 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
   return FFST_OK;
 }
 
-static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, const float* plane_scale, float* img,
-                             cudaStream_t s, bool normalise, bool cplx = false) {
+// Plane passes of the inverse (Sec. 3.3): S_k = sum over the active planes of
+// chunk k of psi_i * fft2(c_i), the half spectrum in the plan's partial
+// accumulators.
+static ffst_status synthesis_planes(ffst_plan_s* p, const void* coeffs, int storage, const float* plane_scale,
+                                    cudaStream_t s, bool cplx) {
   const long long plane = (long long)p->M * p->N;
   const int esz = storage == FFST_STORE_F32 ? 4 : 2;
   const long long spec = (long long)p->M * p->Hc;
@@ -327,13 +332,23 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
     }
   }
   if (e != cudaSuccess) return cuda_fail(e, "inverse plane passes");
-  e = timed(p, kTimeOutCols, 0.0, s, [&] {
-    return cols_fft(p, p->d_S, true, normalise ? p->d_invD : nullptr, s, p->inv_split, spec);
+  return FFST_OK;
+}
+
+// ifft2 of a half spectrum held as nsum partial sums (M x Hc apart) in buf,
+// added in index order, times 1/sum_i psi_i^2 when `normalise`; the column
+// pass works in place in buf.
+static ffst_status synthesis_finish(ffst_plan_s* p, float2* buf, int nsum, bool normalise, float* img,
+                                    cudaStream_t s) {
+  const long long plane = (long long)p->M * p->N;
+  const long long spec = (long long)p->M * p->Hc;
+  cudaError_t e = timed(p, kTimeOutCols, 0.0, s, [&] {
+    return cols_fft(p, buf, true, normalise ? p->d_invD : nullptr, s, nsum, spec);
   });
   if (e != cudaSuccess) return cuda_fail(e, "inverse final column pass");
   C2RArgs oa;
   std::memset(&oa, 0, sizeof(oa));
-  oa.src = p->d_S;
+  oa.src = buf;
   oa.c0 = 0;
   oa.W = p->Hc;
   oa.ld = p->Hc;
@@ -347,6 +362,26 @@ static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, co
   e = timed(p, kTimeOutRows, 4.0 * plane, s, [&] { return rows_c2r(p, oa, 1, s); });
   if (e != cudaSuccess) return cuda_fail(e, "inverse final row pass");
   return FFST_OK;
+}
+
+static ffst_status synthesis(ffst_plan_s* p, const void* coeffs, int storage, const float* plane_scale, float* img,
+                             cudaStream_t s, bool normalise, bool cplx = false) {
+  const ffst_status st = synthesis_planes(p, coeffs, storage, plane_scale, s, cplx);
+  if (st != FFST_OK) return st;
+  return synthesis_finish(p, p->d_S, p->inv_split, normalise, img, s);
+}
+
+// out = sum_k S_k (k = 0 .. nsum-1 in order), n complex values per sum.
+__global__ void k_sum_partials(const float2* __restrict__ S, int nsum, long long n, float2* __restrict__ out) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    float2 acc = __ldcs(&S[i]);
+    for (int k = 1; k < nsum; ++k) {
+      const float2 y = __ldcs(&S[i + k * n]);
+      acc = make_float2(acc.x + y.x, acc.y + y.y);
+    }
+    out[i] = acc;
+  }
 }
 
 }  // namespace ffst
@@ -421,9 +456,56 @@ extern "C" ffst_status ffst_adjoint(ffst_plan_t plan, const void* coeffs, int st
   return synthesis(plan, coeffs, storage, plane_scale, img, static_cast<cudaStream_t>(stream), false);
 }
 
+extern "C" ffst_status ffst_plan_set_planes(ffst_plan_t plan, int p0, int p1) {
+  if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_planes: plan is NULL");
+  if (p0 < 0 || p1 > plan->eta || p0 >= p1)
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_planes: need 0 <= p0 < p1 <= eta, got [" + std::to_string(p0) +
+                                          ", " + std::to_string(p1) + ")");
+  if (plan->sched_mode != 0 && (p0 != 0 || p1 != plan->eta))
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_planes: the persistent schedule runs every plane");
+  if (p0 == plan->pr0 && p1 == plan->pr1) return FFST_OK;
+  cudaError_t e = cudaDeviceSynchronize();  // in-flight transforms use the groups and buffers
+  if (e != cudaSuccess) return cuda_fail(e, "ffst_plan_set_planes");
+  plan->pr0 = p0;
+  plan->pr1 = p1;
+  return plan_regroup(plan, plan->group_mb, plan->group_mb_inv);
+}
+
+extern "C" ffst_status ffst_plan_get_planes(ffst_plan_t plan, int* p0, int* p1) {
+  if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_get_planes: plan is NULL");
+  if (p0) *p0 = plan->pr0;
+  if (p1) *p1 = plan->pr1;
+  return FFST_OK;
+}
+
+extern "C" ffst_status ffst_inverse_partial(ffst_plan_t plan, const void* coeffs, int storage,
+                                            const float* plane_scale, float* spectrum, void* stream) {
+  if (!plan || !coeffs || !spectrum) return fail(FFST_ERR_INVALID_ARG, "ffst_inverse_partial: NULL argument");
+  ffst_status st = check_storage(storage, plane_scale, "ffst_inverse_partial");
+  if (st != FFST_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = synthesis_planes(plan, coeffs, storage, plane_scale, s, false);
+  if (st != FFST_OK) return st;
+  const long long n = (long long)plan->M * plan->Hc;
+  k_sum_partials<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(
+      plan->d_S, plan->inv_split, n, reinterpret_cast<float2*>(spectrum));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "ffst_inverse_partial");
+  return FFST_OK;
+}
+
+extern "C" ffst_status ffst_inverse_finish(ffst_plan_t plan, float* spectrum, int normalise, float* img,
+                                           void* stream) {
+  if (!plan || !spectrum || !img) return fail(FFST_ERR_INVALID_ARG, "ffst_inverse_finish: NULL argument");
+  return synthesis_finish(plan, reinterpret_cast<float2*>(spectrum), 1, normalise != 0, img,
+                          static_cast<cudaStream_t>(stream));
+}
+
 extern "C" ffst_status ffst_plan_set_schedule(ffst_plan_t plan, int mode) {
   if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_schedule: plan is NULL");
   if (mode < 0 || mode > 2) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_schedule: mode must be 0, 1 or 2");
+  if (mode != 0 && (plan->pr0 != 0 || plan->pr1 != plan->eta))
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_schedule: the persistent schedule runs every plane");
   if (mode != 0 && !plan->sched.on && fused_supported(plan->M, plan->N)) {  // built on first use
     const ffst_status st = sched_build(plan, default_ring_mb());
     if (st != FFST_OK) return st;

@@ -271,6 +271,7 @@ struct Sched {
 
 struct ffst_plan_s {
   int M = 0, N = 0, j0 = 0, eta = 0, Hc = 0;
+  int pr0 = 0, pr1 = 0;                 // active plane range [pr0, pr1) of the plane passes (default: all)
   int variant = 0;                      // FFST_VARIANT_CLASSIC or FFST_VARIANT_SMOOTH
   int hm = 0, hn = 0;
   int device = 0;

@@ -311,7 +311,7 @@ static long long build_groups(const ffst_plan_s* p, double mb, std::vector<Group
   off.assign(p->eta, 0);
   auto elems_of = [&](int i) { return (long long)p->M * p->planes[i].ldw; };
   double total = 0.0;
-  for (int i = 0; i < p->eta; ++i) total += (double)elems_of(i);
+  for (int i = p->pr0; i < p->pr1; ++i) total += (double)elems_of(i);
   std::vector<double> cuts;  // group k holds the planes whose midpoint lies in [cuts[k-1], cuts[k])
   if (total > budget) {
     const bool ramp = kGroupRamp < 1.0;
@@ -321,11 +321,11 @@ static long long build_groups(const ffst_plan_s* p, double mb, std::vector<Group
     cuts.push_back(e);
     for (int j = 1; j < (ramp ? k + 1 : k); ++j) cuts.push_back(e + rest * j / k);
   }
-  Group g{0, 0, 0, 0, 0};
+  Group g{p->pr0, p->pr0, 0, p->planes[p->pr0].item0, 0};
   long long maxg = 0;
   double acc = 0.0;
   size_t gk = 0;  // group index of the open group
-  for (int i = 0; i < p->eta; ++i) {
+  for (int i = p->pr0; i < p->pr1; ++i) {
     const long long el = elems_of(i);
     const double mid = acc + 0.5 * (double)el;
     acc += (double)el;
@@ -358,11 +358,12 @@ ffst_status plan_regroup(ffst_plan_s* p, double fwd_mb, double inv_mb) {
   p->d_items = nullptr;
   p->d_partials = nullptr;
   p->d_H = nullptr;
-  // forward column items: the 2-column panels of every plane's slot, in plane order
+  // forward column items: the panels of every active plane's slot, in plane order
   std::vector<ColItem> items;
   for (int i = 0; i < p->eta; ++i) {
     p->planes[i].item0 = (int)items.size();
-    for (int c = p->planes[i].c0al; c < p->planes[i].c0 + p->planes[i].W; c += P) items.push_back(ColItem{i, c});
+    if (i >= p->pr0 && i < p->pr1)
+      for (int c = p->planes[i].c0al; c < p->planes[i].c0 + p->planes[i].W; c += P) items.push_back(ColItem{i, c});
     p->planes[i].nitems = (int)items.size() - p->planes[i].item0;
   }
   p->total_items = (int)items.size();
@@ -508,6 +509,8 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
   p->N = cols;
   p->j0 = j0;
   p->eta = (1 << (j0 + 2)) - 3;  // Sec. 3.5.2
+  p->pr0 = 0;
+  p->pr1 = p->eta;
   p->Hc = cols / 2 + 1;
   p->hm = rows / 2;
   p->hn = cols / 2;
