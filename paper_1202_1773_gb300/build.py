@@ -87,7 +87,7 @@ def build(verbose: bool = False, extra_flags=(), jobs: int | None = None, tag: s
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     objs = [o for o, _ in results]
     if not os.path.exists(lib_path) or any(os.path.getmtime(o) > os.path.getmtime(lib_path) for o in objs):
-        cmd = [nvcc] + ARCH + ["-shared", "-o", lib_path] + objs + ["-lcudart"]
+        cmd = [nvcc] + ARCH + ["-shared", "-o", lib_path] + objs + ["-lcudart", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n$ " + " ".join(cmd) + "\n" + r.stdout + r.stderr)

@@ -10,9 +10,30 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ffst_blue.cuh"
 
 namespace ffst {
+
+// NVTX range around one launch (profilers show the kernel kind and, as the
+// payload, its plane group; -1 outside the group loops).  Header-only NVTX:
+// without an attached tool each call is a null check.
+struct NvtxRange {
+  NvtxRange(const char* name, int group) {
+    nvtxEventAttributes_t a{};
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = name;
+    a.payloadType = NVTX_PAYLOAD_TYPE_INT32;
+    a.payload.iValue = group;
+    nvtxRangePushEx(&a);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 static cudaEvent_t take_event(ffst_plan_s* p) {
   if (!p->timer.pool.empty()) {
@@ -25,9 +46,16 @@ static cudaEvent_t take_event(ffst_plan_s* p) {
   return e;
 }
 
-// Enqueue one launch; with timing on, bracket it with events on its stream.
+static const char* kKindNames[kTimeKinds] = {"img_rows_r2c", "img_cols_fft", "fwd_cols",      "fwd_rows_c2r",
+                                             "inv_rows_r2c", "inv_cols",     "out_cols_ifft", "out_rows_c2r",
+                                             "fwd_fused",    "inv_fused",    "fwd_sched",     "inv_sched",
+                                             "other"};
+
+// Enqueue one launch inside an NVTX range named for its kind (payload: the
+// plane group); with timing on, bracket it with events on its stream.
 template <class F>
-static cudaError_t timed(ffst_plan_s* p, int kind, double bytes, cudaStream_t s, F&& launch) {
+static cudaError_t timed(ffst_plan_s* p, int kind, double bytes, cudaStream_t s, F&& launch, int group = -1) {
+  NvtxRange range(kKindNames[kind], group);
   if (!p->timer.enabled) return launch();
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone) return launch();
@@ -38,11 +66,6 @@ static cudaError_t timed(ffst_plan_s* p, int kind, double bytes, cudaStream_t s,
   p->timer.pending.push_back(Timer::Rec{kind, a, b, bytes});
   return e;
 }
-
-static const char* kKindNames[kTimeKinds] = {"img_rows_r2c", "img_cols_fft", "fwd_cols",      "fwd_rows_c2r",
-                                             "inv_rows_r2c", "inv_cols",     "out_cols_ifft", "out_rows_c2r",
-                                             "fwd_fused",    "inv_fused",    "fwd_sched",     "inv_sched",
-                                             "other"};
 
 static ffst_status check_storage(int storage, const float* scale, const char* fn) {
   if (storage != FFST_STORE_F32 && storage != FFST_STORE_F16 && storage != FFST_STORE_BF16)
@@ -253,7 +276,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
         return launch_fwd_fused(p->M, fwd_cols_args(p, cg, hbuf(p, g), partials, so), cg.nitems,
                                 plane_c2r_args(p, rg, hbuf(p, g - 1), coeffs, storage, plane_scale, so), rg.p1 - rg.p0,
                                 s);
-      });
+      }, (int)g);
       if (e == cudaSuccess) e = scales(g);
     }
     if (e == cudaSuccess) {
@@ -313,7 +336,7 @@ static ffst_status synthesis_planes(ffst_plan_s* p, const void* coeffs, int stor
       e = timed(p, kTimeInvFused, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
         return launch_inv_fused(p->M, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, g), cplx), rg.p1 - rg.p0,
                                 inv_cols_args(p, cg, hbuf(p, g - 1)), s);
-      });
+      }, (int)g);
     }
     if (e == cudaSuccess)
       e = timed(p, kTimeInvCols, 0.0, s, [&] {
@@ -401,6 +424,7 @@ extern "C" ffst_status ffst_forward(ffst_plan_t plan, const float* img, void* co
   if (!plan || !img || !coeffs) return fail(FFST_ERR_INVALID_ARG, "ffst_forward: NULL argument");
   ffst_status st = check_storage(storage, plane_scale, "ffst_forward");
   if (st != FFST_OK) return st;
+  NvtxRange range("ffst_forward", -1);
   return analysis(plan, img, coeffs, storage, plane_scale, static_cast<cudaStream_t>(stream));
 }
 
@@ -445,6 +469,7 @@ extern "C" ffst_status ffst_inverse(ffst_plan_t plan, const void* coeffs, int st
   if (!plan || !coeffs || !img) return fail(FFST_ERR_INVALID_ARG, "ffst_inverse: NULL argument");
   ffst_status st = check_storage(storage, plane_scale, "ffst_inverse");
   if (st != FFST_OK) return st;
+  NvtxRange range("ffst_inverse", -1);
   return synthesis(plan, coeffs, storage, plane_scale, img, static_cast<cudaStream_t>(stream), true);
 }
 
@@ -453,6 +478,7 @@ extern "C" ffst_status ffst_adjoint(ffst_plan_t plan, const void* coeffs, int st
   if (!plan || !coeffs || !img) return fail(FFST_ERR_INVALID_ARG, "ffst_adjoint: NULL argument");
   ffst_status st = check_storage(storage, plane_scale, "ffst_adjoint");
   if (st != FFST_OK) return st;
+  NvtxRange range("ffst_adjoint", -1);
   return synthesis(plan, coeffs, storage, plane_scale, img, static_cast<cudaStream_t>(stream), false);
 }
 
