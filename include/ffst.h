@@ -57,7 +57,8 @@ typedef enum {
   FFST_ERR_UNSUPPORTED_SIZE = 2, /* rows/cols/scales outside the supported set  */
   FFST_ERR_OUT_OF_MEMORY = 3,    /* device or host allocation failed            */
   FFST_ERR_CUDA = 4,             /* a CUDA runtime call failed                  */
-  FFST_ERR_TIMEOUT = 5           /* a bounded device-side wait ran out          */
+  FFST_ERR_TIMEOUT = 5,          /* a bounded device-side wait ran out          */
+  FFST_ERR_BOUNDS = 6            /* a checked build (FFST_CHECK) caught an index outside its buffer */
 } ffst_status;
 
 /* Storage type of a coefficient stack.  Arithmetic is FP32 in every case. */

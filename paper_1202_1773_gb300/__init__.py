@@ -343,7 +343,8 @@ class Plan:
         return ffst_plan_schedule_info(self.handle)
 
     def check(self) -> int:
-        """Synchronise the plan's stream; FFST_ERR_TIMEOUT if a bounded device wait ran out, else 0."""
+        """Synchronise the plan's stream; FFST_ERR_BOUNDS if a checked build caught an index outside its
+        buffer, FFST_ERR_TIMEOUT if a bounded device wait ran out, else 0."""
         return ffst_plan_check(self.handle, self._stream())
 
     # -- timing ---------------------------------------------------------------

@@ -19,6 +19,7 @@ FFST_ERR_UNSUPPORTED_SIZE = 2
 FFST_ERR_OUT_OF_MEMORY = 3
 FFST_ERR_CUDA = 4
 FFST_ERR_TIMEOUT = 5
+FFST_ERR_BOUNDS = 6
 
 FFST_STORE_F32 = 0
 FFST_STORE_F16 = 1
@@ -226,7 +227,7 @@ def ffst_plan_get_schedule(plan: int) -> int:
 
 
 def ffst_plan_check(plan: int, stream: int = 0) -> int:
-    """Status of the bounded device-side waits since the last check (0 = FFST_OK); raises nothing."""
+    """Status of the device-side checks since the last call: FFST_ERR_BOUNDS, FFST_ERR_TIMEOUT or 0; raises nothing."""
     return int(lib().ffst_plan_check(plan, stream))
 
 

@@ -78,13 +78,23 @@ static ffst_status check_storage(int storage, const float* scale, const char* fn
 static float2* hbuf(const ffst_plan_s* p, size_t g) { return p->d_H + (g % 2) * p->h_elems; }
 
 // Fused launches for square images unless FFST_FUSE=0 (separate launches of
-// the same passes, e.g. to time them apart).
+// the same passes, e.g. to time them apart); FFST_FUSE_FWD=0 or 1 overrides
+// the forward alone.
 static bool use_fused(const ffst_plan_s* p) {
   static const bool off = [] {
     const char* e = std::getenv("FFST_FUSE");
     return e && e[0] == '0';
   }();
   return !off && fused_supported(p->M, p->N);
+}
+
+static bool use_fused_fwd(const ffst_plan_s* p) {
+  static const int mode = [] {
+    const char* e = std::getenv("FFST_FUSE_FWD");
+    return e ? (e[0] == '0' ? 0 : 1) : -1;
+  }();
+  if (mode >= 0) return mode == 1 && fused_supported(p->M, p->N);
+  return use_fused(p);
 }
 
 // Persistent schedule when the plan has one and its mode selects it.
@@ -115,7 +125,8 @@ static cudaError_t cols_fft(const ffst_plan_s* p, float2* buf, bool inverse, con
                             int nsum = 1, long long sstride = 0) {
   return p->bl_cols.n
              ? launch_blue_cols_fft(p->bl_cols, buf, p->Hc, p->Hc, inverse, scale_tab, s, nsum, sstride)
-             : launch_cols_fft(p->M, buf, p->Hc, p->Hc, inverse, scale_tab, p->d_tw_cols, s, nsum, sstride);
+             : launch_cols_fft(p->M, buf, p->Hc, p->Hc, inverse, scale_tab, p->d_tw_cols, s, nsum, sstride,
+                               (long long)(nsum > 1 ? nsum : 1) * p->M * p->Hc * (long long)sizeof(float2), p->d_err);
 }
 
 static cudaError_t fwd_cols(const ffst_plan_s* p, const FwdColsArgs& a, int nitems, cudaStream_t s) {
@@ -141,6 +152,9 @@ static FwdColsArgs fwd_cols_args(const ffst_plan_s* p, const Group& g, float2* H
   a.gain = 1.0f / (kR2CGain * (float)p->M * (float)p->N);
   a.tmaps = p->d_tmaps;
   a.odd = (so && so->cplx_part == 1) ? 1 : 0;
+  a.F_bytes = (long long)p->M * p->Hc * (long long)sizeof(float2);
+  a.H_bytes = p->h_elems * (long long)sizeof(float2);
+  a.err = p->d_err;
   return a;
 }
 
@@ -174,6 +188,12 @@ static C2RArgs plane_c2r_args(const ffst_plan_s* p, const Group& g, const float2
     a.dst = static_cast<char*>(coeffs) + ((long long)(g.p0 - p->pr0) * 2 + so->cplx_part) * plane * sizeof(float);
     a.dst_plane_stride = 2 * plane;
   }
+  a.src_bytes = p->h_elems * (long long)sizeof(float2);
+  {  // the planes [g.p0, g.p1) of the caller's stack from a.dst
+    const long long es = a.cplx ? 4 : (storage == FFST_STORE_F32 ? 4 : 2);
+    a.dst_bytes = g.p1 > g.p0 ? ((long long)(g.p1 - g.p0 - 1) * a.dst_plane_stride + plane) * es : 0;
+  }
+  a.err = p->d_err;
   return a;
 }
 
@@ -199,6 +219,12 @@ static R2CArgs plane_r2c_args(const ffst_plan_s* p, const Group& g, const void* 
   a.ld = 0;
   a.tw = p->d_tw_rows;
   a.rtw = p->d_rtw;
+  {  // the planes [g.p0, g.p1) of the caller's stack from a.src
+    const long long es = cplx ? 4 : (storage == FFST_STORE_F32 ? 4 : 2);
+    a.src_bytes = g.p1 > g.p0 ? ((long long)(g.p1 - g.p0 - 1) * a.src_plane_stride + plane) * es : 0;
+  }
+  a.dst_bytes = p->h_elems * (long long)sizeof(float2);
+  a.err = p->d_err;
   return a;
 }
 
@@ -221,6 +247,8 @@ static InvColsArgs inv_cols_args(const ffst_plan_s* p, const Group& g, const flo
   a.tw = p->d_tw_cols;
   a.tmaps = p->d_tmaps_inv;
   a.err = p->d_err;
+  a.H_bytes = p->h_elems * (long long)sizeof(float2);
+  a.S_bytes = (long long)p->inv_split * p->M * p->Hc * (long long)sizeof(float2);
   return a;
 }
 
@@ -241,6 +269,9 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
   ia.ld = p->Hc;
   ia.tw = p->d_tw_rows;
   ia.rtw = p->d_rtw;
+  ia.src_bytes = plane * (long long)sizeof(float);
+  ia.dst_bytes = (long long)p->M * p->Hc * (long long)sizeof(float2);
+  ia.err = p->d_err;
   e = timed(p, kTimeImgRows, 4.0 * plane, s, [&] { return rows_r2c(p, ia, 1, s); });
   if (e != cudaSuccess) return cuda_fail(e, "forward image row pass");
   e = timed(p, kTimeImgCols, 0.0, s,
@@ -263,7 +294,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
                               plane_c2r_args(p, all, nullptr, coeffs, storage, nullptr, so), target,
                               partials ? plane_scale : nullptr, s);
     });
-  } else if (use_fused(p)) {
+  } else if (use_fused_fwd(p)) {
     e = timed(p, kTimeFwdCols, 0.0, s, [&] {
       return fwd_cols(p, fwd_cols_args(p, p->groups[0], hbuf(p, 0), partials, so), p->groups[0].nitems, s);
     });
@@ -382,6 +413,9 @@ static ffst_status synthesis_finish(ffst_plan_s* p, float2* buf, int nsum, bool 
   oa.cplx = 0;
   oa.tw = p->d_tw_rows;
   oa.rtw = p->d_rtw;
+  oa.src_bytes = spec * (long long)sizeof(float2);
+  oa.dst_bytes = plane * (long long)sizeof(float);
+  oa.err = p->d_err;
   e = timed(p, kTimeOutRows, 4.0 * plane, s, [&] { return rows_c2r(p, oa, 1, s); });
   if (e != cudaSuccess) return cuda_fail(e, "inverse final row pass");
   return FFST_OK;
@@ -568,6 +602,9 @@ extern "C" ffst_status ffst_plan_check(ffst_plan_t plan, void* stream) {
   e = cudaMemcpy(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && err) e = cudaMemset(plan->d_err, 0, sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e, "ffst_plan_check");
+  if (err & kErrBounds)
+    return fail(FFST_ERR_BOUNDS, "an index outside its buffer was caught and skipped (FFST_CHECK build); the "
+                                 "transform output is unspecified");
   if (err) return fail(FFST_ERR_TIMEOUT, "a bounded device-side wait ran out; the transform output is unspecified");
   return FFST_OK;
 }

@@ -5,21 +5,21 @@
 namespace ffst {
 
 template <int L, bool INV>
-__global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, min_blocks_for(L))
     k_cols_fft(float2* __restrict__ buf, int width, int ld, const float* __restrict__ scale_tab,
-               const float2* __restrict__ tw, int nsum, long long sstride) {
+               const float2* __restrict__ tw, int nsum, long long sstride, long long buf_bytes, int* err) {
   extern __shared__ __align__(128) float2 smem[];
-  cols_fft_body<L, INV>(buf, width, ld, scale_tab, tw, nsum, sstride, blockIdx.x, smem);
+  cols_fft_body<L, INV>(buf, width, ld, scale_tab, tw, nsum, sstride, blockIdx.x, smem, buf_bytes, err);
 }
 
 template <int L>
-__global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_fwd_cols(FwdColsArgs a) {
+__global__ void __launch_bounds__(kThreads, min_blocks_for(L)) k_fwd_cols(FwdColsArgs a) {
   extern __shared__ __align__(128) float2 smem[];
   fwd_cols_body<L>(a, blockIdx.x, smem);
 }
 
 template <int L>
-__global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_inv_cols(InvColsArgs a) {
+__global__ void __launch_bounds__(kThreads, min_blocks_for(L)) k_inv_cols(InvColsArgs a) {
   extern __shared__ __align__(128) float2 smem[];
   int q0, q1;
   float2* S;
@@ -51,15 +51,18 @@ int cols_per_cta(int L) {
 
 template <int L>
 static cudaError_t cols_fft_L(float2* buf, int width, int ld, bool inverse, const float* scale_tab,
-                              const float2* tw, int nsum, long long sstride, cudaStream_t s) {
+                              const float2* tw, int nsum, long long sstride, long long buf_bytes, int* err,
+                              cudaStream_t s) {
   const int grid = (width + ColCfg<L>::P - 1) / ColCfg<L>::P;
   cudaError_t e;
   if (inverse) {
     if ((e = set_smem(k_cols_fft<L, true>, ColCfg<L>::SMEM)) != cudaSuccess) return e;
-    k_cols_fft<L, true><<<grid, kThreads, ColCfg<L>::SMEM, s>>>(buf, width, ld, scale_tab, tw, nsum, sstride);
+    k_cols_fft<L, true><<<grid, kThreads, ColCfg<L>::SMEM, s>>>(buf, width, ld, scale_tab, tw, nsum, sstride,
+                                                                  buf_bytes, err);
   } else {
     if ((e = set_smem(k_cols_fft<L, false>, ColCfg<L>::SMEM)) != cudaSuccess) return e;
-    k_cols_fft<L, false><<<grid, kThreads, ColCfg<L>::SMEM, s>>>(buf, width, ld, scale_tab, tw, nsum, sstride);
+    k_cols_fft<L, false><<<grid, kThreads, ColCfg<L>::SMEM, s>>>(buf, width, ld, scale_tab, tw, nsum, sstride,
+                                                                   buf_bytes, err);
   }
   return cudaGetLastError();
 }
@@ -107,8 +110,9 @@ static cudaError_t inv_cols_L(const InvColsArgs& a, cudaStream_t s) {
   }
 
 cudaError_t launch_cols_fft(int L, float2* buf, int width, int ld, bool inverse, const float* scale_tab,
-                            const float2* tw, cudaStream_t s, int nsum, long long sstride) {
-#define CALL_(LL) cols_fft_L<LL>(buf, width, ld, inverse, scale_tab, tw, nsum, sstride, s)
+                            const float2* tw, cudaStream_t s, int nsum, long long sstride, long long buf_bytes,
+                            int* err) {
+#define CALL_(LL) cols_fft_L<LL>(buf, width, ld, inverse, scale_tab, tw, nsum, sstride, buf_bytes, err, s)
   FFST_DISPATCH_COL(L, CALL_)
 #undef CALL_
 }

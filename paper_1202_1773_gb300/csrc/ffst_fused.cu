@@ -19,7 +19,7 @@ struct FusedCfg {
 };
 
 template <int M>
-__global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_fwd_fused(FwdColsArgs ca, int nc, C2RArgs ra, int rbx) {
+__global__ void __launch_bounds__(kThreads, min_blocks_for(M)) k_fwd_fused(FwdColsArgs ca, int nc, C2RArgs ra, int rbx) {
   extern __shared__ __align__(128) float2 smem[];
   int ci = 0, ri = 0;
   if (split_cols_first(blockIdx.x, nc, &ci, &ri)) fwd_cols_body<M>(ca, ci, smem);
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_fwd_fused(FwdCols
 }
 
 template <int M>
-__global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_inv_fused(R2CArgs ra, int rbx, InvColsArgs ca, int nc) {
+__global__ void __launch_bounds__(kThreads, min_blocks_for(M)) k_inv_fused(R2CArgs ra, int rbx, InvColsArgs ca, int nc) {
   extern __shared__ __align__(128) float2 smem[];
   int ci = 0, ri = 0;
   if (split_cols_first(blockIdx.x, nc, &ci, &ri)) {

@@ -76,6 +76,11 @@ __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c
 #endif
 __host__ __device__ constexpr bool is_pow2c(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// Resident blocks per SM a column-length-L kernel's register budget is sized
+// for: 4096-point columns hold 32 elements per thread (64 registers of data
+// alone), so their kernels take the budget of two blocks instead of spilling.
+__host__ __device__ constexpr int min_blocks_for(int L) { return L >= 4096 ? 2 : FFST_MIN_BLOCKS; }
+
 // Line lengths with factors 3 or 5 (mixed radix) run 16 or 32 threads per
 // line; powers of two use the register configuration below.
 __host__ __device__ constexpr int mixed_E(int L) { return L / (L <= 256 ? 16 : 32); }

@@ -18,12 +18,13 @@
 //       are dropped (Hermitian part).
 //
 // Column passes (half-spectrum buffers [M][ld], complex, row-major): a block
-// owns a panel of P adjacent columns; thread (t, c) is threadIdx.x = t*P + c,
-// so the P columns of one row are read or written by consecutive lanes.
-// Each column is transformed by the T threads with the same c; their
-// shared-memory exchanges use block barriers.  Within a plane's support
-// column, psi_hat is nonzero only on one cyclic row interval (start, len)
-// computed at plan time; the window is generated and F is read only there.
+// owns a panel of P adjacent columns.  In cols_fft_body and inv_cols_body
+// thread (t, c) is threadIdx.x = t*P + c, so the P columns of one row are
+// read or written by consecutive lanes, and the exchanges use block
+// barriers; fwd_cols_body gives each column a contiguous team of T threads
+// with its own barrier.  Within a plane's support column, psi_hat is nonzero
+// only on one cyclic row interval (start, len) computed at plan time; the
+// window is generated and F is read only there.
 #pragma once
 
 #include "ffst_fft.cuh"
@@ -58,6 +59,39 @@ __device__ __forceinline__ void store_pair(void* p, long long i, float a, float 
 
 // Every half spectrum the row R2C writes is kR2CGain times the DFT.
 constexpr float kR2CGain = 2.0f;
+
+// Bounds checks of the debug build (-DFFST_CHECK): every global access of the
+// transform bodies is tested against its buffer's extent (bytes from the
+// buffer's base, carried in the argument structs).  An access outside is
+// skipped (a load reads zero) and sets kErrBounds in the plan's error word,
+// which ffst_plan_check reports as FFST_ERR_BOUNDS; nothing traps.  In
+// normal builds the checks compile to nothing.
+constexpr int kErrBounds = 8;
+#ifdef FFST_CHECK
+__device__ __forceinline__ bool ck(const void* p, int bytes, const void* base, long long extent, int* err) {
+  const char* q = static_cast<const char*>(p);
+  const char* b = static_cast<const char*>(base);
+  const bool ok = q >= b && q + bytes <= b + extent;
+  if (!ok && err) atomicOr(err, kErrBounds);
+  return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool ck(const void*, int, const void*, long long, int*) { return true; }
+#endif
+
+// load_pair / store_pair checked against [base, base + extent) bytes.
+__device__ __forceinline__ float2 load_pair_ck(const void* p, long long i, int st, const void* base, long long ext,
+                                               int* err) {
+  const int es = stor_bytes(st);
+  if (!ck(static_cast<const char*>(p) + i * es, 2 * es, base, ext, err)) return make_float2(0.f, 0.f);
+  return load_pair(p, i, st);
+}
+__device__ __forceinline__ void store_pair_ck(void* p, long long i, float x, float y, int st, const void* base,
+                                              long long ext, int* err) {
+  const int es = stor_bytes(st);
+  if (ck(static_cast<char*>(p) + i * es, 2 * es, base, ext, err)) store_pair(p, i, x, y, st);
+}
+
 
 // ---------------------------------------------------------------------------
 // geometry
@@ -116,6 +150,9 @@ struct R2CArgs {
   int c0, W, ld;             // used when planes == null
   const float2* tw;          // pass table (L, E)
   const float2* rtw;         // W_N^k, k = 0..L
+  long long src_bytes;       // extents from src and dst (bounds checks of FFST_CHECK builds)
+  long long dst_bytes;
+  int* err;                  // plan error word (FFST_CHECK builds)
 };
 
 template <int L>
@@ -136,16 +173,18 @@ __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, 
   } else if (a.cplx) {  // FP32 real parts of a complex stack, c_i = sqrt(2) Re z_i (i >= 1)
     const float cs = plane == 0 ? 1.0f : 1.41421356237309505f;
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = cscale(load_pair(src, rbase + 2 * T * m, FFST_STORE_F32), cs);
+    for (int m = 0; m < E; ++m)
+      v[m] = cscale(load_pair_ck(src, rbase + 2 * T * m, FFST_STORE_F32, a.src, a.src_bytes, a.err), cs);
   } else if (a.st == FFST_STORE_F32) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = load_pair(src, rbase + 2 * T * m, FFST_STORE_F32);
+    for (int m = 0; m < E; ++m) v[m] = load_pair_ck(src, rbase + 2 * T * m, FFST_STORE_F32, a.src, a.src_bytes, a.err);
   } else {
     const int st = a.st;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      const float2 x = st == FFST_STORE_F16 ? load_pair(src, rbase + 2 * T * m, FFST_STORE_F16)
-                                            : load_pair(src, rbase + 2 * T * m, FFST_STORE_BF16);
+      const float2 x = st == FFST_STORE_F16
+                           ? load_pair_ck(src, rbase + 2 * T * m, FFST_STORE_F16, a.src, a.src_bytes, a.err)
+                           : load_pair_ck(src, rbase + 2 * T * m, FFST_STORE_BF16, a.src, a.src_bytes, a.err);
       v[m] = make_float2(x.x * us, x.y * us);
     }
   }
@@ -170,7 +209,8 @@ __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, 
     const float2 e = make_float2(zk.x + zn.x, zk.y - zn.y);  // 2 E[k]
     const float2 o = make_float2(zk.y + zn.y, zn.x - zk.x);  // 2 O[k]
     const float2 w = __ldg(&a.rtw[k]);
-    __stcg(&drow[idx], make_float2(e.x + w.x * o.x - w.y * o.y, e.y + w.x * o.y + w.y * o.x));
+    if (ck(&drow[idx], 8, a.dst, a.dst_bytes, a.err))
+      __stcg(&drow[idx], make_float2(e.x + w.x * o.x - w.y * o.y, e.y + w.x * o.y + w.y * o.x));
   }
 }
 
@@ -193,6 +233,9 @@ struct C2RArgs {
   float* abs_partials;       // per (plane, row block): sum |c| before shrinkage, or null
   int rbx;                   // row blocks per plane (stride of abs_partials)
   int cplx;                  // complex planar output (Sec. 3.8.2): factor 1/sqrt(2) on planes i >= 1
+  long long src_bytes;       // extents from src and dst (bounds checks of FFST_CHECK builds)
+  long long dst_bytes;
+  int* err;                  // plan error word (FFST_CHECK builds)
 };
 
 // Factor s_i of plane a.plane0 + by for low-precision storage (1 otherwise),
@@ -247,8 +290,10 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
     constexpr int m = decltype(mc)::value;
     const int k = t + T * m;
     const int ia = k - c0, ib = L - k - c0;
-    float2 xa = (act && (unsigned)ia < (unsigned)W) ? __ldcg(&srow[ia]) : make_float2(0.f, 0.f);
-    float2 xb = (act && (unsigned)ib < (unsigned)W) ? __ldcg(&srow[ib]) : make_float2(0.f, 0.f);
+    float2 xa = (act && (unsigned)ia < (unsigned)W && ck(&srow[ia], 8, a.src, a.src_bytes, a.err))
+                    ? __ldcg(&srow[ia]) : make_float2(0.f, 0.f);
+    float2 xb = (act && (unsigned)ib < (unsigned)W && ck(&srow[ib], 8, a.src, a.src_bytes, a.err))
+                    ? __ldcg(&srow[ib]) : make_float2(0.f, 0.f);
     if (m == 0 && t == 0) {  // X[0] and X[N/2]: Hermitian part is real
       xa.y = 0.f;
       xb.y = 0.f;
@@ -301,13 +346,16 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
   const long long rbase = (long long)row * N + 2 * t;
   if (a.st == FFST_STORE_F32) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) store_pair(dst, rbase + 2 * T * m, v[m].x, v[m].y, FFST_STORE_F32);
+    for (int m = 0; m < E; ++m)
+      store_pair_ck(dst, rbase + 2 * T * m, v[m].x, v[m].y, FFST_STORE_F32, a.dst, a.dst_bytes, a.err);
   } else if (a.st == FFST_STORE_F16) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) store_pair(dst, rbase + 2 * T * m, v[m].x, v[m].y, FFST_STORE_F16);
+    for (int m = 0; m < E; ++m)
+      store_pair_ck(dst, rbase + 2 * T * m, v[m].x, v[m].y, FFST_STORE_F16, a.dst, a.dst_bytes, a.err);
   } else {
 #pragma unroll
-    for (int m = 0; m < E; ++m) store_pair(dst, rbase + 2 * T * m, v[m].x, v[m].y, FFST_STORE_BF16);
+    for (int m = 0; m < E; ++m)
+      store_pair_ck(dst, rbase + 2 * T * m, v[m].x, v[m].y, FFST_STORE_BF16, a.dst, a.dst_bytes, a.err);
   }
 }
 
@@ -320,10 +368,13 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
 // elements apart (the inverse's partial accumulators), added in index order
 // and written to the first.  When `scale_tab` is given (same layout), each
 // element is multiplied by it next.
+// buf_bytes: extent of buf and its partial sums (bounds checks of FFST_CHECK
+// builds; scale_tab has the layout of one of them in floats).
 template <int L, bool INV>
 __device__ __forceinline__ void cols_fft_body(float2* __restrict__ buf, int width, int ld,
                                               const float* __restrict__ scale_tab, const float2* __restrict__ tw,
-                                              int nsum, long long sstride, int bx, float2* smem) {
+                                              int nsum, long long sstride, int bx, float2* smem, long long buf_bytes,
+                                              int* err) {
   constexpr int E = ColCfg<L>::E, T = ColCfg<L>::T, P = ColCfg<L>::P;
   const int t = threadIdx.x / P, cl = threadIdx.x % P;
   const int c = bx * P + cl;
@@ -332,24 +383,27 @@ __device__ __forceinline__ void cols_fft_body(float2* __restrict__ buf, int widt
   const long long step = (long long)T * ld;
   float2 v[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[m] = act ? col[m * step] : make_float2(0.f, 0.f);
+  for (int m = 0; m < E; ++m)
+    v[m] = act && ck(&col[m * step], 8, buf, buf_bytes, err) ? col[m * step] : make_float2(0.f, 0.f);
   for (int k = 1; k < nsum && act; ++k) {
     const float2* part = col + k * sstride;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
-      const float2 y = __ldcs(&part[m * step]);
+      const float2 y = ck(&part[m * step], 8, buf, buf_bytes, err) ? __ldcs(&part[m * step]) : make_float2(0.f, 0.f);
       v[m] = make_float2(v[m].x + y.x, v[m].y + y.y);
     }
   }
   if (scale_tab && act) {
     const float* sc = scale_tab + (long long)t * ld + c;
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = cscale(v[m], __ldg(&sc[m * step]));
+    for (int m = 0; m < E; ++m)
+      v[m] = cscale(v[m], ck(&sc[m * step], 4, scale_tab, buf_bytes / 2, err) ? __ldg(&sc[m * step]) : 0.0f);
   }
   line_fft<L, E, INV, kSyncBlock>(v, smem + cl * ColCfg<L>::BUF, t, tw);
   if (act) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) col[m * step] = v[m];
+    for (int m = 0; m < E; ++m)
+      if (ck(&col[m * step], 8, buf, buf_bytes, err)) col[m * step] = v[m];
   }
 }
 
@@ -367,112 +421,106 @@ struct FwdColsArgs {
   float gain;               // G = gain * psi_hat * F (folds the 1/(M N) of the inverse DFT)
   const CUtensorMap* tmaps; // per plane: tensor map of its slot (TMA panel stores), or null
   int odd;                  // one-sided shearlets, imaginary part: G = -i sign(omega) G (Sec. 3.8.2)
+  long long F_bytes;        // extents from F and H (bounds checks of FFST_CHECK builds)
+  long long H_bytes;
+  int* err;                 // plan error word (FFST_CHECK builds)
 };
 
-// Forward column items per block.  A block walks kFwdItems consecutive items
-// and fetches the next item's spectrum values during the current FFT; one
-// item per block measured fastest (2 per block: fewer, longer blocks and a
-// longer launch tail, 1.31 -> 1.44 ms forward at 2048x2048 J=5).
+// Forward column items per block (one: a block's work is one panel).
 constexpr int kFwdItems = 1;
 
 // Forward column pass of plane panels (Sec. 3.1 eq. shearletTransform):
 // G = psi_hat_i * F on the panel's columns, then the column IFFT; the result
 // goes to the plane's slot of the group intermediate, [M][W_i] starting at
-// column c0_i.  The team of a column evaluates psi only on the column's
-// support rows (one cyclic interval, consecutive rows on consecutive
-// threads), reads F only there, and passes G through its shared buffer into
-// the register layout of the FFT.  A thread's first support row of the next
-// item (F value and window) is fetched before the current item's FFT, so
-// its load latency hides behind the transform.  With `partials` the block
-// also writes sum |G| per item, each column counted once for itself and once
-// for its conjugate partner (columns 0 and N/2 are their own partners); a
-// plane's partials add up to sum_omega |G(omega)| >= max_m |c_i(m)| (G
-// carries the 1/(M N) of the inverse DFT through `gain`).
+// column c0_i.  Column cl of the panel belongs to the contiguous team of
+// threads [cl T, (cl + 1) T), which synchronises alone (named barriers), so
+// the P column FFTs of a block do not wait for one another.  Each thread
+// evaluates the window and reads F at its own FFT rows t + T m that lie in
+// the column's support (one cyclic row interval computed at plan time):
+// the spectrum goes straight into the register layout of the FFT, without a
+// shared-memory staging step.  With `partials` the block also writes sum |G|
+// per item, each column counted once for itself and once for its conjugate
+// partner (columns 0 and N/2 are their own partners); a plane's partials add
+// up to sum_omega |G(omega)| >= max_m |c_i(m)| (G carries the 1/(M N) of the
+// inverse DFT through `gain`).
 template <int L>
 __device__ __forceinline__ void fwd_cols_body(const FwdColsArgs& a, int blk, float2* smem) {
   constexpr int E = ColCfg<L>::E, T = ColCfg<L>::T, P = ColCfg<L>::P;
+  constexpr int SYNC = T <= 32 ? kSyncWarp : (T < kThreads ? kSyncNamed : kSyncBlock);
   __shared__ float red[kThreads / 32];
-  const int t = threadIdx.x / P, cl = threadIdx.x % P;
+  const int cl = threadIdx.x / T, t = threadIdx.x % T;
   float2* buf = smem + cl * ColCfg<L>::BUF;
-  const int i0 = blk * kFwdItems;
-  const int i1 = i0 + kFwdItems < a.nitems ? i0 + kFwdItems : a.nitems;
-  // this thread's first support row of item i: F value and window
-  auto prefetch = [&](int i, float2& f, float& psi) {
-    const ColItem it = a.items[i];
-    const PlaneDesc d = a.planes[it.plane];
-    const int c = it.col + cl;
-    const int2 rg = (c >= d.c0 && c < d.c0 + d.W) ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
-    f = make_float2(0.f, 0.f);
-    psi = 0.0f;
-    if (t < rg.y) {
-      const int row = mod_l<L>(rg.x + t);
-      f = a.F[(long long)row * a.Hc + c];
-      psi = win_at(a.w, d, row, c);
-      if (a.odd) psi *= (float)half_sign(a.w, d.kappa, row, c);
-    }
-  };
-  float2 f0;
-  float psi0;
-  if (i0 < i1) prefetch(i0, f0, psi0);
-  for (int item = i0; item < i1; ++item) {
-    const ColItem it = a.items[item];
-    const PlaneDesc d = a.planes[it.plane];
-    const int c = it.col + cl;
-    const bool act = c >= d.c0 && c < d.c0 + d.W;
-    const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
-    float mag = 0.0f;
-    if (t < rg.y) {
-      float2 g = cscale(f0, psi0 * a.gain);
-      if (a.odd) g = make_float2(g.y, -g.x);  // -i g (the sign is in psi0)
-      buf[spad<E>(mod_l<L>(rg.x + t))] = g;
-      if (a.partials) mag += sqrtf(g.x * g.x + g.y * g.y);
-    }
-    for (int q = t + T; q < rg.y; q += T) {
-      const int row = mod_l<L>(rg.x + q);
-      float psi = win_at(a.w, d, row, c);
-      if (a.odd) psi *= (float)half_sign(a.w, d.kappa, row, c);
-      float2 g = make_float2(0.f, 0.f);
-      if (psi != 0.0f) g = cscale(a.F[(long long)row * a.Hc + c], psi * a.gain);
-      if (a.odd) g = make_float2(g.y, -g.x);
-      buf[spad<E>(row)] = g;
-      if (a.partials) mag += sqrtf(g.x * g.x + g.y * g.y);
-    }
+  const int item = blk;  // kFwdItems == 1
+  if (item >= a.nitems) return;  // uniform over the block
+  const ColItem it = a.items[item];
+  const PlaneDesc d = a.planes[it.plane];
+  const int c = it.col + cl;
+  const bool act = c >= d.c0 && c < d.c0 + d.W;
+  const int2 rg = act ? a.rng[d.rng_off + (c - d.c0)] : make_int2(0, 0);
+  float2 v[E];
+  unsigned mask = 0;  // this thread's FFT rows inside the support
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    v[m] = make_float2(0.f, 0.f);
+    if (in_range<L>(t + T * m, rg)) mask |= 1u << m;
+  }
+  float mag = 0.0f;
+  for (unsigned rest = mask; rest; rest &= rest - 1) {  // one copy of the window code
+    const int m = __ffs(rest) - 1;
+    const int row = t + T * m;
+    float psi = win_at(a.w, d, row, c);
+    if (a.odd) psi *= (float)half_sign(a.w, d.kappa, row, c);
+    const float2* fp = a.F + (long long)row * a.Hc + c;
+    float2 g = cscale(ck(fp, 8, a.F, a.F_bytes, a.err) ? *fp : make_float2(0.f, 0.f), psi * a.gain);
+    if (a.odd) g = make_float2(g.y, -g.x);  // -i g (the sign is in psi)
+    if (a.partials) mag += sqrtf(g.x * g.x + g.y * g.y);
+#pragma unroll
+    for (int q = 0; q < E; ++q)
+      if (q == m) v[q] = g;
+  }
+  if (a.partials) {  // fixed reduction order: deterministic
+    const bool self_partner = (c == 0) || (2 * c == a.w.N);
+    mag *= self_partner ? 1.0f : 2.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mag += __shfl_xor_sync(0xffffffffu, mag, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mag;
+  }
+  line_fft<L, E, true, SYNC>(v, buf, t, a.tw, 1 + cl);
+  if (a.tmaps) {
+    // the panel [L][P] through shared memory (aliasing the FFT buffers, which
+    // every team has finished with at the block barrier) and one TMA store;
+    // columns outside the support store zeros
     __syncthreads();
-    float2 v[E];
+    float2* tile = smem;
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int row = t + T * m;
-      v[m] = in_range<L>(row, rg) ? buf[spad<E>(row)] : make_float2(0.f, 0.f);
+    for (int m = 0; m < E; ++m) tile[(t + T * m) * P + cl] = act ? v[m] : make_float2(0.f, 0.f);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (a.partials) {
+        float sum = 0.0f;
+        for (int q = 0; q < kThreads / 32; ++q) sum += red[q];
+        a.partials[item] = sum;
+      }
+      tma_store_panel(&a.tmaps[it.plane], tile, 2 * (it.col - d.c0al));
     }
+    __syncthreads();  // the copy has read the panel before the buffers are reused
+  } else {
     if (a.partials) {
-      const bool self_partner = (c == 0) || (2 * c == a.w.N);
-      mag *= self_partner ? 1.0f : 2.0f;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mag += __shfl_xor_sync(0xffffffffu, mag, o);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mag;
-    }
-    __syncthreads();  // buf reads done (and red written) before the FFT reuses buf
-    if (a.partials && threadIdx.x == 0) {
-      float sum = 0.0f;
-      for (int q = 0; q < kThreads / 32; ++q) sum += red[q];
-      a.partials[item] = sum;
-    }
-    if (item + 1 < i1) prefetch(item + 1, f0, psi0);
-    line_fft<L, E, true, kSyncBlock>(v, buf, t, a.tw);  // ends with a barrier after its last buf read
-    if (a.tmaps) {
-      // the panel [L][P] through shared memory (aliasing the free FFT
-      // buffers) and one TMA store; columns outside the support store zeros
-      float2* tile = smem;
-#pragma unroll
-      for (int m = 0; m < E; ++m) tile[(t + T * m) * P + cl] = act ? v[m] : make_float2(0.f, 0.f);
-      fence_proxy_async_smem();
       __syncthreads();
-      if (threadIdx.x == 0) tma_store_panel(&a.tmaps[it.plane], tile, 2 * (it.col - d.c0al));
-      __syncthreads();  // the copy has read the panel before the buffers are reused
-    } else if (act) {
+      if (threadIdx.x == 0) {
+        float sum = 0.0f;
+        for (int q = 0; q < kThreads / 32; ++q) sum += red[q];
+        a.partials[item] = sum;
+      }
+    }
+    if (act) {
       float2* out = a.H + d.off + (c - d.c0al);
 #pragma unroll
-      for (int m = 0; m < E; ++m) __stcg(&out[(long long)(t + T * m) * d.ldw], v[m]);
+      for (int m = 0; m < E; ++m) {
+        float2* o = &out[(long long)(t + T * m) * d.ldw];
+        if (ck(o, 8, a.H, a.H_bytes, a.err)) __stcg(o, v[m]);
+      }
     }
   }
 }
@@ -491,7 +539,9 @@ struct InvColsArgs {
   WinParams w;
   const float2* tw;
   const CUtensorMap* tmaps; // per plane: tensor map of its slot (TMA panel loads), or null
-  int* err;                 // sticky error word (a TMA wait that ran out sets bit 2)
+  int* err;                 // sticky error word (a TMA wait that ran out sets bit 2; FFST_CHECK: kErrBounds)
+  long long H_bytes;        // extents from H and S (bounds checks of FFST_CHECK builds)
+  long long S_bytes;
 };
 
 // Block bx of an inverse column launch (npanels x nchunks blocks): panel
@@ -540,7 +590,10 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, int 
     const bool act = c >= c0 && c < c0 + W;
     const float2* in = a.H + a.planes[p].off + (c - a.planes[p].c0al);
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = act ? __ldcg(&in[(long long)(t + T * m) * ldw]) : make_float2(0.f, 0.f);
+    for (int m = 0; m < E; ++m) {
+      const float2* q = &in[(long long)(t + T * m) * ldw];
+      v[m] = act && ck(q, 8, a.H, a.H_bytes, a.err) ? __ldcg(q) : make_float2(0.f, 0.f);
+    }
   };
   // TMA: the panel [L][P] of plane p into shared memory (aliasing the FFT
   // buffers); x may be negative (leading columns read as zeros)
@@ -578,7 +631,8 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, int 
       float2 s0 = make_float2(0.f, 0.f);
       float psi0 = 0.0f;
       if (mask) {  // first row's accumulator and window, ahead of the FFT
-        s0 = __ldcg(&S[(long long)row0 * a.Hc + c]);
+        const float2* sp0 = &S[(long long)row0 * a.Hc + c];
+        s0 = ck(sp0, 8, a.S, a.S_bytes, a.err) ? __ldcg(sp0) : make_float2(0.f, 0.f);
         psi0 = win_at(a.w, d, row0, c);
       }
       if (!__syncthreads_and(mbar_wait(&mbar, phase, a.err))) return;
@@ -591,13 +645,15 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, int 
       if (pn < p1) issue_panel(pn);
       if (mask) {
         const float2 x = pick(v, m0);
-        S[(long long)row0 * a.Hc + c] = make_float2(fmaf(psi0, x.x, s0.x), fmaf(psi0, x.y, s0.y));
+        float2* sp0 = &S[(long long)row0 * a.Hc + c];
+        if (ck(sp0, 8, a.S, a.S_bytes, a.err)) *sp0 = make_float2(fmaf(psi0, x.x, s0.x), fmaf(psi0, x.y, s0.y));
         for (unsigned rest = mask & (mask - 1); rest; rest &= rest - 1) {
           const int m = __ffs(rest) - 1;
           const int row = t + T * m;
           const float psi = win_at(a.w, d, row, c);
           const float2 y = pick(v, m);
           float2* sp = S + (long long)row * a.Hc + c;
+          if (!ck(sp, 8, a.S, a.S_bytes, a.err)) continue;
           const float2 old = __ldcg(sp);
           *sp = make_float2(fmaf(psi, y.x, old.x), fmaf(psi, y.y, old.y));
         }
@@ -612,7 +668,8 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, int 
     float2 s0 = make_float2(0.f, 0.f);
     float psi0 = 0.0f;
     if (first) {
-      s0 = __ldcg(&S[(long long)row0 * a.Hc + c]);
+      const float2* sp0 = &S[(long long)row0 * a.Hc + c];
+      s0 = ck(sp0, 8, a.S, a.S_bytes, a.err) ? __ldcg(sp0) : make_float2(0.f, 0.f);
       psi0 = win_at(a.w, d, row0, c);
     }
     line_fft<L, E, false, kSyncBlock>(v, buf, t, a.tw);
@@ -626,13 +683,15 @@ __device__ __forceinline__ void inv_cols_body(const InvColsArgs& a, int bx, int 
     __syncthreads();
     if (first) {
       const float2 x = buf[spad<E>(row0)];
-      S[(long long)row0 * a.Hc + c] = make_float2(fmaf(psi0, x.x, s0.x), fmaf(psi0, x.y, s0.y));
+      float2* sp0 = &S[(long long)row0 * a.Hc + c];
+      if (ck(sp0, 8, a.S, a.S_bytes, a.err)) *sp0 = make_float2(fmaf(psi0, x.x, s0.x), fmaf(psi0, x.y, s0.y));
     }
     for (int q = t + T; q < rg.y; q += T) {
       const int row = mod_l<L>(rg.x + q);
       const float psi = win_at(a.w, d, row, c);
       const float2 x = buf[spad<E>(row)];
       float2* sp = S + (long long)row * a.Hc + c;
+      if (!ck(sp, 8, a.S, a.S_bytes, a.err)) continue;
       const float2 old = __ldcg(sp);
       *sp = make_float2(fmaf(psi, x.x, old.x), fmaf(psi, x.y, old.y));
     }
@@ -657,7 +716,8 @@ __device__ __forceinline__ bool split_cols_first(int b, int nc, int* ci, int* ri
 cudaError_t launch_rows_r2c(int L, const R2CArgs& a, int nplanes, cudaStream_t s);
 cudaError_t launch_rows_c2r(int L, const C2RArgs& a, int nplanes, cudaStream_t s);
 cudaError_t launch_cols_fft(int L, float2* buf, int width, int ld, bool inverse, const float* scale_tab,
-                            const float2* tw, cudaStream_t s, int nsum = 1, long long sstride = 0);
+                            const float2* tw, cudaStream_t s, int nsum, long long sstride, long long buf_bytes,
+                            int* err);
 cudaError_t launch_fwd_cols(int L, const FwdColsArgs& a, int nitems, cudaStream_t s);
 cudaError_t launch_inv_cols(int L, const InvColsArgs& a, cudaStream_t s);  // a.npanels x a.nchunks blocks
 // Fused launches exist for square power-of-two images with 256 <= M <= 4096

@@ -278,8 +278,12 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
   ia.ld = P.Hc;
   ia.tw = P.d_tw_rows;
   ia.rtw = P.d_rtw;
+  ia.src_bytes = plane * (long long)sizeof(float);
+  ia.dst_bytes = (long long)rows * P.Hc * (long long)sizeof(float2);
   e = launch_rows_r2c(cols / 2, ia, 1, s);
-  if (e == cudaSuccess) e = launch_cols_fft(rows, P.d_F, P.Hc, P.Hc, false, nullptr, P.d_tw_cols, s);
+  if (e == cudaSuccess)
+    e = launch_cols_fft(rows, P.d_F, P.Hc, P.Hc, false, nullptr, P.d_tw_cols, s, 1, 0,
+                        (long long)rows * P.Hc * (long long)sizeof(float2), nullptr);
   for (int p0 = 0; p0 < P.eta && e == cudaSuccess; p0 += kNaGroup) {
     const int p1 = p0 + kNaGroup < P.eta ? p0 + kNaGroup : P.eta;
     FwdColsArgs ca;
@@ -295,6 +299,9 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
     ca.gain = 1.0f / (kR2CGain * (float)plane);
     ca.tmaps = nullptr;
     ca.odd = 0;
+    ca.F_bytes = (long long)rows * P.Hc * (long long)sizeof(float2);
+    ca.H_bytes = kNaGroup * kNaSlot * (long long)sizeof(float2);
+    ca.err = nullptr;
     e = launch_fwd_cols(rows, ca, (p1 - p0) * su.ipp, s);
     if (e != cudaSuccess) break;
     C2RArgs ra;
@@ -309,6 +316,8 @@ extern "C" ffst_status ffst_forward_noalloc(int rows, int cols, int scales, cons
     ra.scale = 1.0f;
     ra.tw = P.d_tw_rows;
     ra.rtw = P.d_rtw;
+    ra.src_bytes = kNaGroup * kNaSlot * (long long)sizeof(float2);
+    ra.dst_bytes = (long long)(p1 - p0) * plane * (long long)sizeof(float);
     e = launch_rows_c2r(cols / 2, ra, p1 - p0, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "ffst_forward_noalloc: transform");

@@ -103,19 +103,40 @@ static double varphi_sig64(double w, const VSpec& vs) {
 // ---------------------------------------------------------------------------
 
 // For every plane, the smallest and largest half-spectrum column where the
-// spectrum is nonzero (minmax[2i], minmax[2i+1]).
-__global__ void k_support(WinParams w, const PlaneDesc* __restrict__ planes, int eta, int Hc, int* minmax) {
-  const long long per_plane = (long long)w.M * Hc;
-  const long long total = per_plane * eta;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / per_plane);
-    const long long rem = idx - (long long)i * per_plane;
-    const int pr = (int)(rem / Hc), pc = (int)(rem % Hc);
-    const PlaneDesc d = planes[i];
+// spectrum is nonzero (minmax[2i], minmax[2i+1]).  Block (plane i, row
+// chunk): each thread keeps its own extremes over its elements, a block
+// reduction leaves one atomic pair per block.
+__global__ void k_support(WinParams w, const PlaneDesc* __restrict__ planes, int Hc, int rows_per_block,
+                          int* minmax) {
+  __shared__ int smin[32], smax[32];
+  const int i = blockIdx.y;
+  const PlaneDesc d = planes[i];
+  const int r0 = blockIdx.x * rows_per_block;
+  const int r1 = min(w.M, r0 + rows_per_block);
+  int lo = 0x7fffffff, hi = -1;
+  for (int e = threadIdx.x; e < (r1 - r0) * Hc; e += blockDim.x) {
+    const int pr = r0 + e / Hc, pc = e % Hc;
     if (win_at(w, d, pr, pc) != 0.0f) {
-      atomicMin(&minmax[2 * i], pc);
-      atomicMax(&minmax[2 * i + 1], pc);
+      lo = min(lo, pc);
+      hi = max(hi, pc);
+    }
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    smin[wid] = lo;
+    smax[wid] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < nw; ++q) {
+      lo = min(lo, smin[q]);
+      hi = max(hi, smax[q]);
+    }
+    if (hi >= 0) {
+      atomicMin(&minmax[2 * i], lo);
+      atomicMax(&minmax[2 * i + 1], hi);
     }
   }
 }
@@ -144,36 +165,64 @@ cudaError_t launch_spectra(const ffst_plan_s* p, float* psi, cudaStream_t s) {
 }
 
 cudaError_t launch_support(const ffst_plan_s* p, int* d_minmax, cudaStream_t s) {
-  k_support<<<152 * 8, 256, 0, s>>>(p->win, p->d_planes, p->eta, p->Hc, d_minmax);
+  // about 64K window values per block
+  const int rpb = std::max(1, (1 << 16) / p->Hc);
+  const dim3 grid((p->M + rpb - 1) / rpb, p->eta);
+  k_support<<<grid, 256, 0, s>>>(p->win, p->d_planes, p->Hc, rpb, d_minmax);
   return cudaGetLastError();
 }
 
 // For every plane and support column, the shortest cyclic row interval
 // (start, len) that holds all nonzero rows: the complement of the largest
-// cyclic gap between consecutive nonzero rows.  One CTA per plane.
+// cyclic gap between consecutive nonzero rows.  One warp per (plane, support
+// column) (blockIdx.y = plane): lane l scans the rows [l M/32, (l+1) M/32) in
+// order (first and last nonzero row, largest inner gap), then lane 0 joins
+// the 32 chunks in row order, as one sequential scan over all rows would.
 __global__ void k_ranges(WinParams w, const PlaneDesc* __restrict__ planes, int2* __restrict__ rng) {
-  const PlaneDesc d = planes[blockIdx.x];
-  for (int q = threadIdx.x; q < d.W; q += blockDim.x) {
-    const int c = d.c0 + q;
-    int first = -1, prev = -1, maxgap = -1, after = 0;
-    for (int r = 0; r < w.M; ++r) {
-      if (win_at(w, d, r, c) != 0.0f) {
-        if (first < 0) {
-          first = r;
-        } else {
-          const int gap = r - prev - 1;
-          if (gap > maxgap) {
-            maxgap = gap;
-            after = r;
-          }
-        }
-        prev = r;
+  const PlaneDesc d = planes[blockIdx.y];
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (q >= d.W) return;  // whole warps
+  const int lane = threadIdx.x & 31;
+  const int c = d.c0 + q;
+  const int chunk = (w.M + 31) / 32;
+  const int ra = lane * chunk, rb = min(w.M, ra + chunk);
+  int first = -1, prev = -1, maxgap = -1, after = 0;
+  for (int r = ra; r < rb; ++r) {
+    if (win_at(w, d, r, c) != 0.0f) {
+      if (first < 0) {
+        first = r;
+      } else if (r - prev - 1 > maxgap) {
+        maxgap = r - prev - 1;
+        after = r;
       }
+      prev = r;
     }
+  }
+  // join the chunks in order on lane 0 (same result as one scan over 0..M-1)
+  int gfirst = -1, gprev = -1, gmax = -1, gafter = 0;
+  for (int l = 0; l < 32; ++l) {
+    const int f = __shfl_sync(0xffffffffu, first, l);
+    const int p = __shfl_sync(0xffffffffu, prev, l);
+    const int g = __shfl_sync(0xffffffffu, maxgap, l);
+    const int a = __shfl_sync(0xffffffffu, after, l);
+    if (f < 0) continue;
+    if (gfirst < 0) {
+      gfirst = f;
+    } else if (f - gprev - 1 > gmax) {
+      gmax = f - gprev - 1;
+      gafter = f;
+    }
+    if (g > gmax) {
+      gmax = g;
+      gafter = a;
+    }
+    gprev = p;
+  }
+  if (lane == 0) {
     int2 out = make_int2(0, 0);
-    if (first >= 0) {
-      const int wrap = first + w.M - prev - 1;
-      out = (wrap >= maxgap) ? make_int2(first, prev - first + 1) : make_int2(after, w.M - maxgap);
+    if (gfirst >= 0) {
+      const int wrap = gfirst + w.M - gprev - 1;
+      out = (wrap >= gmax) ? make_int2(gfirst, gprev - gfirst + 1) : make_int2(gafter, w.M - gmax);
     }
     rng[d.rng_off + q] = out;
   }
@@ -207,7 +256,10 @@ __global__ void k_inv_norm(WinParams w, const PlaneDesc* __restrict__ planes, in
 }
 
 cudaError_t launch_ranges(const ffst_plan_s* p, cudaStream_t s) {
-  k_ranges<<<p->eta, 256, 0, s>>>(p->win, p->d_planes, p->d_rng);
+  int wmax = 1;
+  for (const PlaneDesc& d : p->planes) wmax = std::max(wmax, d.W);
+  const dim3 grid((wmax + 7) / 8, p->eta);  // 8 warps per block, one per support column
+  k_ranges<<<grid, 256, 0, s>>>(p->win, p->d_planes, p->d_rng);
   return cudaGetLastError();
 }
 
@@ -749,6 +801,7 @@ extern "C" const char* ffst_status_string(int status) {
     case FFST_ERR_OUT_OF_MEMORY: return "FFST_ERR_OUT_OF_MEMORY";
     case FFST_ERR_CUDA: return "FFST_ERR_CUDA";
     case FFST_ERR_TIMEOUT: return "FFST_ERR_TIMEOUT";
+    case FFST_ERR_BOUNDS: return "FFST_ERR_BOUNDS";
     default: return "FFST_ERR_UNKNOWN";
   }
 }

@@ -1,7 +1,42 @@
-// Standalone row-pass kernels (bodies in ffst_kernels.cuh) and their launchers.
-#include "ffst_kernels.cuh"
+// Standalone row-pass kernels (bodies in ffst_kernels.cuh and
+// ffst_rows_pair.cuh) and their launchers.
+#include <cstdlib>
+
+#include "ffst_rows_pair.cuh"
 
 namespace ffst {
+
+// Paired-row C2R (two rows per team, packed FP32 pairs) for power-of-two
+// half lengths 256..2048 when FFST_PAIR_ROWS=1.  Off by default: at 2048x2048
+// it measured 0.737 against 0.672 ms per forward's row passes (half the
+// resident warps at 128 registers cost more than the halved FP instructions
+// save).
+static bool pair_rows_on(int L) {
+  static const bool on = [] {
+    const char* e = std::getenv("FFST_PAIR_ROWS");
+    return e && e[0] == '1';
+  }();
+  return on && is_pow2c(L) && L >= 256 && L <= 2048;
+}
+
+template <int L>
+__global__ void __launch_bounds__(kThreads, 2) k_rows_c2r_pair(C2RArgs a) {
+  extern __shared__ __align__(128) float4 smem4[];
+  rows_c2r_pair_body<L>(a, blockIdx.x, blockIdx.y, smem4, c2r_plane_factor(a, blockIdx.y));
+}
+
+template <int L>
+static cudaError_t c2r_pair_L(const C2RArgs& a, int nplanes, cudaStream_t s) {
+  if constexpr (is_pow2c(L) && L >= 256 && L <= 2048) {
+    const dim3 grid((a.M + RowPairCfg<L>::ROWS - 1) / RowPairCfg<L>::ROWS, nplanes);
+    cudaError_t e = set_smem(k_rows_c2r_pair<L>, RowPairCfg<L>::SMEM);
+    if (e != cudaSuccess) return e;
+    k_rows_c2r_pair<L><<<grid, kThreads, RowPairCfg<L>::SMEM, s>>>(a);
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
 
 template <int L>
 __global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_rows_r2c(R2CArgs a) {
@@ -26,6 +61,7 @@ static cudaError_t r2c_L(const R2CArgs& a, int nplanes, cudaStream_t s) {
 
 template <int L>
 static cudaError_t c2r_L(const C2RArgs& a, int nplanes, cudaStream_t s) {
+  if (pair_rows_on(L)) return c2r_pair_L<L>(a, nplanes, s);
   const dim3 grid((a.M + RowCfg<L>::TEAMS - 1) / RowCfg<L>::TEAMS, nplanes);
   cudaError_t e = set_smem(k_rows_c2r<L>, RowCfg<L>::SMEM);
   if (e != cudaSuccess) return e;

@@ -302,8 +302,10 @@ cudaError_t launch_fwd_sched(const ffst_plan_s* p, FwdColsArgs ca, C2RArgs ra, f
   ca.H = sc.d_ring;
   ca.partials = scale_out ? p->d_partials : nullptr;
   ca.tmaps = nullptr;  // the maps describe the group buffers, not the ring
+  ca.H_bytes = sc.ring_elems * (long long)sizeof(float2);
   ra.plane_scale = nullptr;  // the kernel passes the plane factor itself
   ra.src = sc.d_ring;
+  ra.src_bytes = sc.ring_elems * (long long)sizeof(float2);
   ra.planes = sc.d_planes;
   ra.plane0 = 0;
 #define CALL_(MM) fwd_sched_M<MM>(sc, s, ca, ra, st)
@@ -322,6 +324,8 @@ cudaError_t launch_inv_sched(const ffst_plan_s* p, R2CArgs ra, InvColsArgs ca, c
   ca.H = sc.d_ring;
   ca.planes = sc.d_planes;
   ca.tmaps = nullptr;  // the maps describe the group buffers, not the ring
+  ra.dst_bytes = sc.ring_elems * (long long)sizeof(float2);
+  ca.H_bytes = sc.ring_elems * (long long)sizeof(float2);
 #define CALL_(MM) inv_sched_M<MM>(sc, s, ra, ca, st)
   FFST_DISPATCH_SCHED(p->M, CALL_)
 #undef CALL_

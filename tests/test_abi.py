@@ -106,3 +106,27 @@ def test_batch_and_graph_argument_errors_on_host(lib):
     assert lib.ffst_plan_group_mb(None, None, None) == _lib.FFST_ERR_INVALID_ARG
     lib.ffst_graph_destroy(None)
     lib.ffst_batch_destroy(None)
+
+
+def test_checked_build_compiles():
+    # the bounds-checked debug build (-DFFST_CHECK) of the instrumented
+    # transform bodies compiles for sm_103a: the fused launches hold all four
+    # plane-pass bodies (the whole checked build runs on the GPU in
+    # tests/test_gpu_check.py)
+    import shutil
+    import subprocess
+    import tempfile
+
+    from paper_1202_1773_gb300 import build
+
+    try:
+        nvcc = build.nvcc_path()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+    with tempfile.TemporaryDirectory() as d:
+        for unit in ("ffst_fused.cu",):
+            src = os.path.join(build.CSRC, unit)
+            cmd = [nvcc] + build._flags(["-DFFST_CHECK"]) + ["-c", src, "-o", os.path.join(d, unit + ".o")]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            assert r.returncode == 0, r.stderr[-3000:]
+    assert shutil.which(nvcc) or os.path.exists(nvcc)
