@@ -243,20 +243,46 @@ ffst_status ffst_adjoint(ffst_plan_t plan, const void* coeffs, int storage,
 ffst_status ffst_forward_noalloc(int rows, int cols, int scales, const float* img, float* coeffs, void* stream);
 
 /*
- * Autotune a plan's launch configuration for coefficient storage `storage`:
- * for each candidate plane-group budget (32, 64, 96, 128, 192 MB of
- * column-pass intermediates per fused launch) times `reps` forwards and
- * inverses (after one warm-up round trip), the two directions apart, and
- * keeps the fastest budget for each.  Allocates a temporary image and
- * coefficient stack of the plan's size (eta*rows*cols elements) and
- * synchronises the device.  When the environment variable
- * FFST_AUTOTUNE_CACHE names a file, the choice is appended to it and later
- * ffst_plan calls for the same device and shape start from it.  Results do
- * not depend on the budgets.  *fwd_mb and *inv_mb (either may be NULL)
- * receive the choice.  The budgets only matter for grouped launches
- * (schedule mode 0, the default).
+ * Autotune a plan's launch configuration for coefficient storage `storage`,
+ * each direction apart, on the plan's own shape (`reps` timed calls per
+ * candidate after one warm-up):
+ *   1. the plane-group budget: 32, 64, 96, 128 or 192 MB of column-pass
+ *      intermediates per launch;
+ *   2. at those budgets, the kernel configuration (ffst_plan_set_kernels):
+ *      fused plane-pass launches (square powers of two) or separate row and
+ *      column launches with each row-FFT variant that exists for the row
+ *      length, and for the inverse also 1, 2, 4 or the default number of
+ *      plane chunks of its sum.
+ * Keeps the fastest of each.  Allocates a temporary image and coefficient
+ * stack of the plan's size (eta*rows*cols elements) and synchronises the
+ * device.  When the environment variable FFST_AUTOTUNE_CACHE names a file,
+ * the choice is appended to it and later ffst_plan calls for the same device
+ * and shape start from it.  The budgets and the fusion choice do not change
+ * results; the row variants and the plane chunks change only the rounding
+ * order.  *fwd_mb and *inv_mb (either may be NULL) receive the budgets.  The
+ * choices only matter for grouped launches (schedule mode 0, the default).
  */
 ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int reps, double* fwd_mb, double* inv_mb);
+
+/*
+ * Kernel configuration of a plan (what ffst_plan_autotune chooses):
+ *   fuse_fwd, fuse_inv  1: one launch per plane group holds the column pass
+ *                       of that group and the row pass of the previous one
+ *                       (square power-of-two images only; ignored otherwise);
+ *                       0: separate row and column launches;
+ *   row_fwd, row_inv    the FFT of the separate row launches: 0 = 16 elements
+ *                       per thread (radix 16 x 16 x 4 at 1024-point lines,
+ *                       two shared-memory exchanges); 1 = two rows per team
+ *                       with packed two-lane FP32 arithmetic (forward only,
+ *                       power-of-two widths 512..4096); 2 = 32 elements per
+ *                       thread (radix 32 x 32, one exchange; widths 2048 and
+ *                       4096).  Fused launches use 0.
+ * The same transform in every configuration (the row variants differ in
+ * rounding only).  FFST_ERR_INVALID_ARG for flags other than 0/1 or a row
+ * variant the plan's width does not have.
+ */
+ffst_status ffst_plan_set_kernels(ffst_plan_t plan, int fuse_fwd, int fuse_inv, int row_fwd, int row_inv);
+ffst_status ffst_plan_get_kernels(ffst_plan_t plan, int* fuse_fwd, int* fuse_inv, int* row_fwd, int* row_inv);
 
 /* The plane-group budgets (MB) of the plan's forward and inverse. */
 ffst_status ffst_plan_group_mb(ffst_plan_t plan, double* fwd_mb, double* inv_mb);

@@ -153,6 +153,16 @@ class Plan:
     def full_shape(self):
         return (self.num_planes, self.rows, self.cols)
 
+    @property
+    def kernels(self):
+        """(fuse_fwd, fuse_inv, row_fwd, row_inv): the kernel configuration (ffst_plan_get_kernels)."""
+        return _lib.ffst_plan_get_kernels(self.handle)
+
+    def set_kernels(self, fuse_fwd: int = 1, fuse_inv: int = 1, row_fwd: int = 0, row_inv: int = 0):
+        """Fused launches per direction and the row-FFT variant of separate row
+        launches (ffst_plan_set_kernels)."""
+        _lib.ffst_plan_set_kernels(self.handle, fuse_fwd, fuse_inv, row_fwd, row_inv)
+
     def set_planes(self, p0: int, p1: int):
         """Restrict the transforms to the planes [p0, p1) (ffst_plan_set_planes):
         stacks then hold those planes only, plane p0 first."""

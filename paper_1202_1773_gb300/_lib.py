@@ -49,6 +49,9 @@ SIGNATURES = [
     ("ffst_plan_get_schedule", _I, [_VP, ctypes.POINTER(_I)]),
     ("ffst_plan_set_inverse_split", _I, [_VP, _I]),
     ("ffst_plan_set_planes", _I, [_VP, _I, _I]),
+    ("ffst_plan_set_kernels", _I, [_VP, _I, _I, _I, _I]),
+    ("ffst_plan_get_kernels", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                   ctypes.POINTER(_I)]),
     ("ffst_plan_get_planes", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     ("ffst_inverse_partial", _I, [_VP, _VP, _I, _VP, _VP, _VP]),
     ("ffst_inverse_finish", _I, [_VP, _VP, _I, _VP, _VP]),
@@ -233,6 +236,17 @@ def ffst_plan_check(plan: int, stream: int = 0) -> int:
 
 def ffst_plan_set_inverse_split(plan: int, nsplit: int):
     _check("ffst_plan_set_inverse_split", lib().ffst_plan_set_inverse_split(plan, int(nsplit)))
+
+
+def ffst_plan_set_kernels(plan: int, fuse_fwd: int, fuse_inv: int, row_fwd: int, row_inv: int):
+    _check("ffst_plan_set_kernels", lib().ffst_plan_set_kernels(plan, int(fuse_fwd), int(fuse_inv), int(row_fwd),
+                                                                int(row_inv)))
+
+
+def ffst_plan_get_kernels(plan: int):
+    v = [_I() for _ in range(4)]
+    _check("ffst_plan_get_kernels", lib().ffst_plan_get_kernels(plan, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def ffst_plan_set_planes(plan: int, p0: int, p1: int):

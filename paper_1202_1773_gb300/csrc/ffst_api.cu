@@ -77,28 +77,28 @@ static ffst_status check_storage(int storage, const float* scale, const char* fn
 
 static float2* hbuf(const ffst_plan_s* p, size_t g) { return p->d_H + (g % 2) * p->h_elems; }
 
-// Fused launches for square images unless FFST_FUSE=0 (separate launches of
-// the same passes, e.g. to time them apart); FFST_FUSE_FWD=0 or 1 overrides
-// the forward alone.
-static bool use_fused(const ffst_plan_s* p) {
-  static const bool off = [] {
-    const char* e = std::getenv("FFST_FUSE");
-    return e && e[0] == '0';
-  }();
-  return !off && fused_supported(p->M, p->N);
-}
+// Fused plane-pass launches (square powers of two) per direction, as the
+// plan's kernel configuration selects (ffst_plan_set_kernels).
+static bool use_fused(const ffst_plan_s* p) { return p->fuse_inv && fused_supported(p->M, p->N); }
+static bool use_fused_fwd(const ffst_plan_s* p) { return p->fuse_fwd && fused_supported(p->M, p->N); }
 
-static bool use_fused_fwd(const ffst_plan_s* p) {
-  static const int mode = [] {
-    const char* e = std::getenv("FFST_FUSE_FWD");
-    return e ? (e[0] == '0' ? 0 : 1) : -1;
-  }();
-  if (mode >= 0) return mode == 1 && fused_supported(p->M, p->N);
-  return use_fused(p);
-}
+
 
 // Persistent schedule when the plan has one and its mode selects it.
 static bool use_sched(const ffst_plan_s* p) { return p->sched.on && p->sched_mode != 0; }
+
+// Row kernel variant of a direction's standalone plane row passes; the fused
+// and persistent launches (and so the standalone edge groups of a fused
+// schedule) use 0.
+static int fwd_row_variant(const ffst_plan_s* p) {
+  return use_fused_fwd(p) || use_sched(p) || p->bl_rows.n ? 0 : p->row_fwd;
+}
+static int inv_row_variant(const ffst_plan_s* p) {
+  return use_fused(p) || use_sched(p) || p->bl_rows.n ? 0 : p->row_inv;
+}
+static const float2* row_table(const ffst_plan_s* p, int variant) {
+  return variant == 2 ? p->d_tw_rows32 : p->d_tw_rows;
+}
 
 static Group all_planes(const ffst_plan_s* p) { return Group{p->pr0, p->pr1, 0, 0, p->total_items}; }
 
@@ -113,12 +113,14 @@ struct StatsOpts {
 // Line passes at the plan's sizes: native FFT lines, or generic (Bluestein)
 // lines for a dimension without them (ffst_blue.cuh).  Generic sizes never
 // take the fused or persistent launches (fused_supported).
-static cudaError_t rows_r2c(const ffst_plan_s* p, const R2CArgs& a, int nplanes, cudaStream_t s) {
-  return p->bl_rows.n ? launch_blue_rows_r2c(p->bl_rows, a, nplanes, s) : launch_rows_r2c(p->N / 2, a, nplanes, s);
+static cudaError_t rows_r2c(const ffst_plan_s* p, const R2CArgs& a, int nplanes, cudaStream_t s, int variant = 0) {
+  return p->bl_rows.n ? launch_blue_rows_r2c(p->bl_rows, a, nplanes, s)
+                      : launch_rows_r2c(p->N / 2, a, nplanes, s, variant);
 }
 
-static cudaError_t rows_c2r(const ffst_plan_s* p, const C2RArgs& a, int nplanes, cudaStream_t s) {
-  return p->bl_rows.n ? launch_blue_rows_c2r(p->bl_rows, a, nplanes, s) : launch_rows_c2r(p->N / 2, a, nplanes, s);
+static cudaError_t rows_c2r(const ffst_plan_s* p, const C2RArgs& a, int nplanes, cudaStream_t s, int variant = 0) {
+  return p->bl_rows.n ? launch_blue_rows_c2r(p->bl_rows, a, nplanes, s)
+                      : launch_rows_c2r(p->N / 2, a, nplanes, s, variant);
 }
 
 static cudaError_t cols_fft(const ffst_plan_s* p, float2* buf, bool inverse, const float* scale_tab, cudaStream_t s,
@@ -176,7 +178,7 @@ static C2RArgs plane_c2r_args(const ffst_plan_s* p, const Group& g, const float2
   a.st = storage;
   a.plane_scale = plane_scale;
   a.scale = 1.0f;  // fwd_cols already applied 1/(M N) (and the R2C gain)
-  a.tw = p->d_tw_rows;
+  a.tw = row_table(p, fwd_row_variant(p));
   a.rtw = p->d_rtw;
   a.shrink = so ? so->shrink : 0;
   a.thresh = so ? so->thresh : nullptr;
@@ -217,7 +219,7 @@ static R2CArgs plane_r2c_args(const ffst_plan_s* p, const Group& g, const void* 
   a.c0 = 0;
   a.W = 0;
   a.ld = 0;
-  a.tw = p->d_tw_rows;
+  a.tw = row_table(p, inv_row_variant(p));
   a.rtw = p->d_rtw;
   {  // the planes [g.p0, g.p1) of the caller's stack from a.src
     const long long es = cplx ? 4 : (storage == FFST_STORE_F32 ? 4 : 2);
@@ -314,7 +316,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
       const Group& rg = p->groups[G - 1];
       e = timed(p, kTimeFwdRows, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
         return rows_c2r(p, plane_c2r_args(p, rg, hbuf(p, G - 1), coeffs, storage, plane_scale, so),
-                               rg.p1 - rg.p0, s);
+                               rg.p1 - rg.p0, s, fwd_row_variant(p));
       });
     }
   } else {
@@ -328,7 +330,7 @@ static ffst_status analysis(ffst_plan_s* p, const float* img, void* coeffs, int 
       if (e == cudaSuccess)
         e = timed(p, kTimeFwdRows, (double)(gr.p1 - gr.p0) * plane * esz, s, [&] {
           return rows_c2r(p, plane_c2r_args(p, gr, hbuf(p, g), coeffs, storage, plane_scale, so), gr.p1 - gr.p0,
-                                 s);
+                                 s, fwd_row_variant(p));
         });
     }
   }
@@ -358,7 +360,7 @@ static ffst_status synthesis_planes(ffst_plan_s* p, const void* coeffs, int stor
       const Group& rg = p->groups_inv[0];
       e = timed(p, kTimeInvRows, (double)(rg.p1 - rg.p0) * plane * esz, s, [&] {
         return rows_r2c(p, plane_r2c_args(p, rg, coeffs, storage, plane_scale, hbuf(p, 0), cplx), rg.p1 - rg.p0,
-                               s);
+                               s, inv_row_variant(p));
       });
     }
     for (size_t g = 1; g < G && e == cudaSuccess; ++g) {
@@ -378,7 +380,7 @@ static ffst_status synthesis_planes(ffst_plan_s* p, const void* coeffs, int stor
       const Group& gr = p->groups_inv[g];
       e = timed(p, kTimeInvRows, (double)(gr.p1 - gr.p0) * plane * esz, s, [&] {
         return rows_r2c(p, plane_r2c_args(p, gr, coeffs, storage, plane_scale, hbuf(p, g), cplx), gr.p1 - gr.p0,
-                               s);
+                               s, inv_row_variant(p));
       });
       if (e == cudaSuccess)
         e = timed(p, kTimeInvCols, 0.0, s,
@@ -514,6 +516,34 @@ extern "C" ffst_status ffst_adjoint(ffst_plan_t plan, const void* coeffs, int st
   if (st != FFST_OK) return st;
   NvtxRange range("ffst_adjoint", -1);
   return synthesis(plan, coeffs, storage, plane_scale, img, static_cast<cudaStream_t>(stream), false);
+}
+
+extern "C" ffst_status ffst_plan_set_kernels(ffst_plan_t plan, int fuse_fwd, int fuse_inv, int row_fwd, int row_inv) {
+  if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_kernels: plan is NULL");
+  if ((fuse_fwd | fuse_inv) & ~1) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_kernels: fuse flags are 0 or 1");
+  const int L = plan->N / 2;
+  const bool native = plan->bl_rows.n == 0;
+  if (!(row_fwd == 0 || (native && row_variant_ok(L, row_fwd, true))))
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_kernels: row variant " + std::to_string(row_fwd) +
+                                          " does not exist for forward rows of length " + std::to_string(plan->N));
+  if (!(row_inv == 0 || (native && row_variant_ok(L, row_inv, false))))
+    return fail(FFST_ERR_INVALID_ARG, "ffst_plan_set_kernels: row variant " + std::to_string(row_inv) +
+                                          " does not exist for inverse rows of length " + std::to_string(plan->N));
+  plan->fuse_fwd = fuse_fwd;
+  plan->fuse_inv = fuse_inv;
+  plan->row_fwd = row_fwd;
+  plan->row_inv = row_inv;
+  return FFST_OK;
+}
+
+extern "C" ffst_status ffst_plan_get_kernels(ffst_plan_t plan, int* fuse_fwd, int* fuse_inv, int* row_fwd,
+                                             int* row_inv) {
+  if (!plan) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_get_kernels: plan is NULL");
+  if (fuse_fwd) *fuse_fwd = plan->fuse_fwd;
+  if (fuse_inv) *fuse_inv = plan->fuse_inv;
+  if (row_fwd) *row_fwd = plan->row_fwd;
+  if (row_inv) *row_inv = plan->row_inv;
+  return FFST_OK;
 }
 
 extern "C" ffst_status ffst_plan_set_planes(ffst_plan_t plan, int p0, int p1) {

@@ -1,14 +1,21 @@
-// Autotuner of a plan's launch configuration.
+// Autotuner of a plan's launch configuration, per shape and storage type.
 //
-// The knob with the largest measured effect is the plane-group budget (how
-// many planes' column-pass intermediates one fused launch holds): larger
-// groups mean fewer launches and shorter tails, smaller groups keep more of
-// the intermediates in L2.  ffst_plan_autotune times the forward and the
-// inverse of a round trip apart for each candidate budget on the plan's own
-// shape and keeps the fastest for each direction.  With FFST_AUTOTUNE_CACHE
-// set, results are appended to that text file ("<device> <rows> <cols>
-// <scales> <storage> <forward MB> <inverse MB>" per line) and ffst_plan reads
-// them back, so a shape is tuned once per machine.
+// Stage 1, the plane-group budget (how many planes' column-pass
+// intermediates one fused launch holds): larger groups mean fewer launches
+// and shorter tails, smaller groups keep more of the intermediates in L2.
+// Stage 2, at those budgets, the kernel configuration of each direction:
+// fused plane-pass launches or separate row and column launches, and for
+// separate launches the row-FFT tile and radix schedule (ffst_rows.cu
+// variants: 16 elements per thread with radix 16 x 16 x 4 at length 1024,
+// two rows per team in packed FP32 pairs, or 32 elements per thread with
+// radix 32 x 32 and one exchange); for the inverse also the number of plane
+// chunks of its sum.  Every candidate is timed on the plan's own shape, the
+// forward and the inverse apart, and the fastest kept.  With
+// FFST_AUTOTUNE_CACHE set, results are appended to that text file, one line
+// "<device> <rows> <cols> <scales> <storage> <forward MB> <inverse MB>
+// <fuse fwd> <row fwd> <fuse inv> <row inv> <inverse chunks>", and
+// ffst_plan reads them back, so a shape is tuned once per machine (lines
+// with only the two budgets are read as well).
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
@@ -38,7 +45,7 @@ static std::string plan_key(const ffst_plan_s* p, int storage) {
   return os.str();
 }
 
-bool autotune_lookup(const ffst_plan_s* p, int storage, double* fwd_mb, double* inv_mb) {
+bool autotune_lookup(const ffst_plan_s* p, int storage, TuneConfig* cfg) {
   const std::string path = cache_path();
   if (path.empty()) return false;
   std::lock_guard<std::mutex> lock(g_cache_mutex);
@@ -50,10 +57,17 @@ bool autotune_lookup(const ffst_plan_s* p, int storage, double* fwd_mb, double* 
   while (std::getline(in, line)) {
     if (line.compare(0, key.size() + 1, key + " ") != 0) continue;
     std::istringstream rest(line.substr(key.size() + 1));
-    double f = 0.0, i = 0.0;
-    if (!(rest >> f >> i) || f <= 0.0 || i <= 0.0) continue;
-    *fwd_mb = f;  // the last entry for a key wins
-    *inv_mb = i;
+    TuneConfig c;
+    if (!(rest >> c.fwd_mb >> c.inv_mb) || c.fwd_mb <= 0.0 || c.inv_mb <= 0.0) continue;
+    int ff = -1, rf = -1, fi = -1, ri = -1, ns = -1;
+    if (rest >> ff >> rf >> fi >> ri >> ns) {
+      c.fuse_fwd = ff;
+      c.row_fwd = rf;
+      c.fuse_inv = fi;
+      c.row_inv = ri;
+      c.inv_split = ns;
+    }
+    *cfg = c;  // the last entry for a key wins
     found = true;
   }
   return found;
@@ -64,7 +78,9 @@ static void autotune_store(const ffst_plan_s* p, int storage, double fwd_mb, dou
   if (path.empty()) return;
   std::lock_guard<std::mutex> lock(g_cache_mutex);
   std::ofstream out(path, std::ios::app);
-  if (out) out << plan_key(p, storage) << ' ' << fwd_mb << ' ' << inv_mb << '\n';
+  if (out)
+    out << plan_key(p, storage) << ' ' << fwd_mb << ' ' << inv_mb << ' ' << p->fuse_fwd << ' ' << p->row_fwd << ' '
+        << p->fuse_inv << ' ' << p->row_inv << ' ' << p->inv_split << '\n';
 }
 
 }  // namespace ffst
@@ -140,8 +156,76 @@ extern "C" ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int rep
       best_i = mb;
     }
   }
+  ffst_status st = plan_regroup(p, best_f, best_i);
+  if (st != FFST_OK) {
+    p->timer.enabled = was_timing;
+    cleanup();
+    return st;
+  }
+
+  // stage 2: kernel configuration of each direction at the chosen budgets
+  auto time_dir = [&](bool fwd) -> float {  // summed ms of reps calls after one warm-up; < 0 on failure
+    float tot = 0.f;
+    for (int q = 0; q < 1 + reps; ++q) {
+      cudaEventRecord(ev[0], s);
+      const bool ok = fwd ? ffst_forward(p, img, coeffs, storage, scale, s) == FFST_OK
+                          : ffst_inverse(p, coeffs, storage, scale, out, s) == FFST_OK;
+      cudaEventRecord(ev[1], s);
+      if (!ok || cudaEventSynchronize(ev[1]) != cudaSuccess) return -1.f;
+      float a = 0.f;
+      cudaEventElapsedTime(&a, ev[0], ev[1]);
+      if (q > 0) tot += a;
+    }
+    return tot;
+  };
+  const int L = p->N / 2;
+  const bool native = p->bl_rows.n == 0;
+  const bool fusable = fused_supported(p->M, p->N);
+  struct Cand {
+    int fuse, row, split;
+  };
+  std::vector<Cand> fc;
+  if (fusable) fc.push_back({1, 0, 0});
+  for (int v = 0; v <= 2; ++v)
+    if (v == 0 || (native && row_variant_ok(L, v, true))) fc.push_back({0, v, 0});
+  Cand bf = {p->fuse_fwd, p->row_fwd, 0};
+  float tb = 1e30f;
+  for (const Cand& c : fc) {
+    p->fuse_fwd = c.fuse;
+    p->row_fwd = c.row;
+    const float t = time_dir(true);
+    if (t >= 0.f && t < tb) {
+      tb = t;
+      bf = c;
+    }
+  }
+  p->fuse_fwd = bf.fuse;
+  p->row_fwd = bf.row;
+  std::vector<int> splits = {p->inv_split_default};
+  for (int n : {1, 2, 4})
+    if (n != p->inv_split_default) splits.push_back(n);
+  std::vector<Cand> ic;
+  for (int n : splits) {
+    if (fusable) ic.push_back({1, 0, n});
+    for (int v = 0; v <= 2; ++v)
+      if (v == 0 || (native && row_variant_ok(L, v, false))) ic.push_back({0, v, n});
+  }
+  Cand bi = {p->fuse_inv, p->row_inv, p->inv_split};
+  tb = 1e30f;
+  for (const Cand& c : ic) {
+    p->fuse_inv = c.fuse;
+    p->row_inv = c.row;
+    if (plan_set_inv_split(p, c.split) != FFST_OK) continue;
+    const float t = time_dir(false);
+    if (t >= 0.f && t < tb) {
+      tb = t;
+      bi = c;
+    }
+  }
+  p->fuse_inv = bi.fuse;
+  p->row_inv = bi.row;
+  st = plan_set_inv_split(p, bi.split);
   p->timer.enabled = was_timing;
-  const ffst_status st = plan_regroup(p, best_f, best_i);
   cleanup();
   if (st != FFST_OK) return st;
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "ffst_plan_autotune");

@@ -285,6 +285,13 @@ struct ffst_plan_s {
   float* d_tables = nullptr;            // psi1_col | psi1_row | phi_col | phi_row
   ffst::WinParams win{};
   float2* d_tw_rows = nullptr;          // pass twiddles of the row lines (N/2, row_E)
+  float2* d_tw_rows32 = nullptr;        // pass twiddles of 32-element row lines (N/2 = 1024, 2048 only)
+  // kernel configuration (ffst_plan_set_kernels, ffst_plan_autotune): fused
+  // plane-pass launches per direction, and the row kernel variant of the
+  // standalone row passes (0 default, 1 paired rows, 2 32 elements per thread;
+  // the fused launches always use variant 0)
+  int fuse_fwd = 1, fuse_inv = 1;
+  int row_fwd = 0, row_inv = 0;
   float2* d_rtw = nullptr;              // exp(-2 pi i k / N), k = 0..N/2 (real-FFT split)
   float2* d_tw_cols = nullptr;          // pass twiddles of the column lines (M, col_E)
   int2* d_rng = nullptr;                // per (plane, support column): cyclic row range (start, len)
@@ -334,7 +341,18 @@ ffst_status plan_regroup(ffst_plan_s* p, double fwd_mb, double inv_mb);
 constexpr int kMaxInvSplit = 16;
 int inv_part(const ffst_plan_s* p, int plane);
 ffst_status plan_set_inv_split(ffst_plan_s* p, int n);
-bool autotune_lookup(const ffst_plan_s* p, int storage, double* fwd_mb, double* inv_mb);
+// A tuned configuration of one plan shape (ffst_plan_autotune's cache entry).
+struct TuneConfig {
+  double fwd_mb = 0.0, inv_mb = 0.0;        // plane-group budgets
+  int fuse_fwd = -1, fuse_inv = -1;         // -1: not in the entry (keep the defaults)
+  int row_fwd = -1, row_inv = -1;
+  int inv_split = -1;
+};
+bool autotune_lookup(const ffst_plan_s* p, int storage, TuneConfig* cfg);
+// row kernel variant v (ffst_rows.cu) exists for half-length L
+bool row_variant_ok(int L, int variant, bool c2r);
+// fused plane-pass launches exist for this shape (ffst_fused.cu)
+bool fused_supported(int M, int N);
 
 // timing helpers
 void timer_begin(ffst_plan_s* p, int kind, cudaStream_t s, double bytes, cudaEvent_t* out_b);

@@ -96,10 +96,13 @@ __device__ __forceinline__ void store_pair_ck(void* p, long long i, float x, flo
 // ---------------------------------------------------------------------------
 // geometry
 // ---------------------------------------------------------------------------
-template <int L>
+// Row-line geometry with EL elements per thread (default row_E(L)); the
+// 32-element variant of the long lines (radix 32 x 32 at L = 1024, one warp
+// per line) is a tuning choice of the standalone row kernels.
+template <int L, int EL = row_E(L)>
 struct RowCfg {
   static_assert(supported_line(L), "unsupported row line length");
-  static constexpr int E = row_E(L);
+  static constexpr int E = EL;
   static constexpr int T = L / E;
   static constexpr int TEAMS = (T >= kThreads) ? 1 : kThreads / T;  // rows per block
   static constexpr int SYNC = T <= 32 ? kSyncWarp : (T < kThreads ? kSyncNamed : kSyncBlock);
@@ -155,13 +158,14 @@ struct R2CArgs {
   int* err;                  // plan error word (FFST_CHECK builds)
 };
 
-template <int L>
+template <int L, int EL = row_E(L)>
 __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, float2* smem) {
-  constexpr int E = RowCfg<L>::E, T = RowCfg<L>::T, N = 2 * L;
+  using C = RowCfg<L, EL>;
+  constexpr int E = C::E, T = C::T, N = 2 * L;
   const int team = threadIdx.x / T, t = threadIdx.x % T;
-  float2* buf = smem + team * RowCfg<L>::BUF;
+  float2* buf = smem + team * C::BUF;
   const int plane = a.plane0 + by;
-  const int row = bx * RowCfg<L>::TEAMS + team;
+  const int row = bx * C::TEAMS + team;
   const bool act = row < a.M;
   const void* src = static_cast<const char*>(a.src) + (long long)by * a.src_plane_stride * stor_bytes(a.st);
   const float us = (a.st != FFST_STORE_F32 && a.plane_scale) ? 1.0f / __ldg(&a.plane_scale[plane]) : 1.0f;
@@ -188,9 +192,9 @@ __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, 
       v[m] = make_float2(x.x * us, x.y * us);
     }
   }
-  line_fft<L, E, false, RowCfg<L>::SYNC>(v, buf, t, a.tw, 1 + team);
+  line_fft<L, E, false, C::SYNC>(v, buf, t, a.tw, 1 + team);
   team_store<E, T>(buf, t, v);
-  team_sync<RowCfg<L>::SYNC, T>(1 + team);
+  team_sync<C::SYNC, T>(1 + team);
   if (!act) return;
   int c0 = a.c0, W = a.W, ld = a.ld;
   float2* dst = a.dst;
@@ -262,13 +266,16 @@ __device__ __forceinline__ float plane_scale_of(const float* partials, int item0
 }
 
 // `ps` is the plane factor s_i multiplied into the output (c2r_plane_factor).
-template <int L>
+// The statistics partials always cover RowCfg<L>::TEAMS rows (the default
+// geometry), so a block of another geometry writes TEAMS / that of them.
+template <int L, int EL = row_E(L)>
 __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, float2* smem, float ps) {
-  constexpr int E = RowCfg<L>::E, T = RowCfg<L>::T, N = 2 * L;
+  using C = RowCfg<L, EL>;
+  constexpr int E = C::E, T = C::T, N = 2 * L;
   const int team = threadIdx.x / T, t = threadIdx.x % T;
-  float2* buf = smem + team * RowCfg<L>::BUF;
+  float2* buf = smem + team * C::BUF;
   const int plane = a.plane0 + by;
-  const int row = bx * RowCfg<L>::TEAMS + team;
+  const int row = bx * C::TEAMS + team;
   const bool act = row < a.M;
   int c0 = a.c0, W = a.W, ld = a.ld;
   const float2* src = a.src;
@@ -308,7 +315,7 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = make_float2(v[m].x * s, v[m].y * s);
   }
-  line_fft<L, E, true, RowCfg<L>::SYNC>(v, buf, t, a.tw, 1 + team);
+  line_fft<L, E, true, C::SYNC>(v, buf, t, a.tw, 1 + team);
   if (a.shrink || a.abs_partials) {  // uniform over the launch
     // v holds c * ps: threshold and statistics act on c (ps is a power of two)
     __shared__ float red[kThreads / 32];
@@ -330,14 +337,16 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
       }
     }
     if (a.abs_partials) {  // fixed reduction order: deterministic
+      constexpr int ratio = C::TEAMS / RowCfg<L>::TEAMS;  // partials per block
+      constexpr int wpp = kThreads / 32 / ratio;          // warps per partial
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
       __syncthreads();
-      if (threadIdx.x == 0) {
+      if (threadIdx.x < ratio) {
         float sum = 0.0f;
-        for (int q = 0; q < kThreads / 32; ++q) sum += red[q];
-        a.abs_partials[(long long)plane * a.rbx + bx] = sum / ps;
+        for (int q = 0; q < wpp; ++q) sum += red[threadIdx.x * wpp + q];
+        a.abs_partials[(long long)plane * a.rbx + bx * ratio + threadIdx.x] = sum / ps;
       }
     }
   }
@@ -713,8 +722,10 @@ __device__ __forceinline__ bool split_cols_first(int b, int nc, int* ci, int* ri
 // ---------------------------------------------------------------------------
 // launchers (ffst_rows.cu, ffst_cols.cu, ffst_fused.cu)
 // ---------------------------------------------------------------------------
-cudaError_t launch_rows_r2c(int L, const R2CArgs& a, int nplanes, cudaStream_t s);
-cudaError_t launch_rows_c2r(int L, const C2RArgs& a, int nplanes, cudaStream_t s);
+// `variant`: the row kernel variant (ffst_rows.cu; 0 = RowCfg<L>); Args.tw must
+// be the pass table of that variant's elements per thread.
+cudaError_t launch_rows_r2c(int L, const R2CArgs& a, int nplanes, cudaStream_t s, int variant = 0);
+cudaError_t launch_rows_c2r(int L, const C2RArgs& a, int nplanes, cudaStream_t s, int variant = 0);
 cudaError_t launch_cols_fft(int L, float2* buf, int width, int ld, bool inverse, const float* scale_tab,
                             const float2* tw, cudaStream_t s, int nsum, long long sstride, long long buf_bytes,
                             int* err);

@@ -296,6 +296,7 @@ static void free_plan(ffst_plan_s* p) {
   cudaFree(p->d_planes_inv);
   cudaFree(p->d_tables);
   cudaFree(p->d_tw_rows);
+  cudaFree(p->d_tw_rows32);
   cudaFree(p->d_tw_cols);
   cudaFree(p->d_rtw);
   cudaFree(p->d_blue);
@@ -653,6 +654,9 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
   // twiddles (FP64 -> FP32): row lines of length N/2, their real split, column lines of length M
   if (nat_rows) {
     if ((e = upload(&p->d_tw_rows, pass_table(cols / 2, row_E(cols / 2)))) != cudaSuccess) return cuda_fail(e, "twiddles");
+    if (row_variant_ok(cols / 2, 2, true) &&
+        (e = upload(&p->d_tw_rows32, pass_table(cols / 2, 32))) != cudaSuccess)
+      return cuda_fail(e, "twiddles");
     if ((e = upload(&p->d_rtw, real_twiddles(cols))) != cudaSuccess) return cuda_fail(e, "twiddles");
   }
   if (nat_cols) {
@@ -730,12 +734,23 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
     if (e != cudaSuccess) return cuda_fail(e, "ffst_plan row ranges");
   }
 
-  // groups and forward column work items (budgets: autotune cache, FFST_GROUP_MB*, defaults)
+  // kernel configuration and groups (autotune cache, else FFST_GROUP_MB* and defaults)
+  TuneConfig tc;
+  const bool tuned = autotune_lookup(p.get(), FFST_STORE_F32, &tc);
   {
-    double fmb = 0.0, imb = 0.0;
-    if (!autotune_lookup(p.get(), FFST_STORE_F32, &fmb, &imb)) default_group_mb(&fmb, &imb);
+    double fmb = tc.fwd_mb, imb = tc.inv_mb;
+    if (!tuned) default_group_mb(&fmb, &imb);
     const ffst_status st = plan_regroup(p.get(), fmb, imb);
     if (st != FFST_OK) return st;
+    const int L = cols / 2;
+    if (tc.fuse_fwd >= 0) p->fuse_fwd = tc.fuse_fwd;
+    if (tc.fuse_inv >= 0) p->fuse_inv = tc.fuse_inv;
+    if (nat_rows && tc.row_fwd >= 0 && row_variant_ok(L, tc.row_fwd, true)) p->row_fwd = tc.row_fwd;
+    if (nat_rows && tc.row_inv >= 0 && row_variant_ok(L, tc.row_inv, false)) p->row_inv = tc.row_inv;
+    // FFST_FUSE=0 (both directions) and FFST_FUSE_FWD=0/1 override the fused launches (A/B timing)
+    if (const char* f = std::getenv("FFST_FUSE"))
+      if (f[0] == '0') p->fuse_fwd = p->fuse_inv = 0;
+    if (const char* f = std::getenv("FFST_FUSE_FWD")) p->fuse_fwd = f[0] == '0' ? 0 : 1;
   }
 
   // workspace
@@ -756,7 +771,8 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
   }
   {
     p->inv_split_default = default_inv_split(p.get());
-    const ffst_status st = plan_set_inv_split(p.get(), p->inv_split_default);
+    const int ns = (tuned && tc.inv_split >= 1 && tc.inv_split <= kMaxInvSplit) ? tc.inv_split : p->inv_split_default;
+    const ffst_status st = plan_set_inv_split(p.get(), ns);
     if (st != FFST_OK) return st;
   }
   if ((e = cudaMalloc(&p->d_invD, spec * sizeof(float))) != cudaSuccess) return cuda_fail(e, "normalisation");

@@ -1,22 +1,24 @@
 // Standalone row-pass kernels (bodies in ffst_kernels.cuh and
 // ffst_rows_pair.cuh) and their launchers.
-#include <cstdlib>
-
+//
+// Row kernel variants, a per-plan tuning choice (ffst_plan_set_kernels):
+//  0  RowCfg<L>: 16 elements per thread for L >= 16 (radix 16 x 16 x 4 at
+//     L = 1024; 64-register budget, 4 blocks per SM);
+//  1  paired rows (C2R only): two rows per team in packed FP32 pairs,
+//     power-of-two L in 256..2048 (ffst_rows_pair.cuh);
+//  2  32 elements per thread, L = 1024 and 2048 (radix 32 x 32 at L = 1024:
+//     one warp per line and one shared-memory exchange; budget of 3 blocks).
+// Every variant computes the same transform; only the operation order of
+// the FFT (and with it the rounding) differs.
 #include "ffst_rows_pair.cuh"
 
 namespace ffst {
 
-// Paired-row C2R (two rows per team, packed FP32 pairs) for power-of-two
-// half lengths 256..2048 when FFST_PAIR_ROWS=1.  Off by default: at 2048x2048
-// it measured 0.737 against 0.672 ms per forward's row passes (half the
-// resident warps at 128 registers cost more than the halved FP instructions
-// save).
-static bool pair_rows_on(int L) {
-  static const bool on = [] {
-    const char* e = std::getenv("FFST_PAIR_ROWS");
-    return e && e[0] == '1';
-  }();
-  return on && is_pow2c(L) && L >= 256 && L <= 2048;
+bool row_variant_ok(int L, int variant, bool c2r) {
+  if (variant == 0) return true;
+  if (variant == 1) return c2r && is_pow2c(L) && L >= 256 && L <= 2048;
+  if (variant == 2) return L == 1024 || L == 2048;
+  return false;
 }
 
 template <int L>
@@ -38,35 +40,55 @@ static cudaError_t c2r_pair_L(const C2RArgs& a, int nplanes, cudaStream_t s) {
   }
 }
 
-template <int L>
-__global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_rows_r2c(R2CArgs a) {
+template <int L, int EL>
+__global__ void __launch_bounds__(kThreads, EL >= 32 ? 3 : FFST_MIN_BLOCKS) k_rows_r2c(R2CArgs a) {
   extern __shared__ __align__(128) float2 smem[];
-  rows_r2c_body<L>(a, blockIdx.x, blockIdx.y, smem);
+  rows_r2c_body<L, EL>(a, blockIdx.x, blockIdx.y, smem);
 }
 
-template <int L>
-__global__ void __launch_bounds__(kThreads, FFST_MIN_BLOCKS) k_rows_c2r(C2RArgs a) {
+template <int L, int EL>
+__global__ void __launch_bounds__(kThreads, EL >= 32 ? 3 : FFST_MIN_BLOCKS) k_rows_c2r(C2RArgs a) {
   extern __shared__ __align__(128) float2 smem[];
-  rows_c2r_body<L>(a, blockIdx.x, blockIdx.y, smem, c2r_plane_factor(a, blockIdx.y));
+  rows_c2r_body<L, EL>(a, blockIdx.x, blockIdx.y, smem, c2r_plane_factor(a, blockIdx.y));
 }
 
-template <int L>
-static cudaError_t r2c_L(const R2CArgs& a, int nplanes, cudaStream_t s) {
-  const dim3 grid((a.M + RowCfg<L>::TEAMS - 1) / RowCfg<L>::TEAMS, nplanes);
-  cudaError_t e = set_smem(k_rows_r2c<L>, RowCfg<L>::SMEM);
+template <int L, int EL>
+static cudaError_t r2c_LE(const R2CArgs& a, int nplanes, cudaStream_t s) {
+  using C = RowCfg<L, EL>;
+  const dim3 grid((a.M + C::TEAMS - 1) / C::TEAMS, nplanes);
+  cudaError_t e = set_smem(k_rows_r2c<L, EL>, C::SMEM);
   if (e != cudaSuccess) return e;
-  k_rows_r2c<L><<<grid, kThreads, RowCfg<L>::SMEM, s>>>(a);
+  k_rows_r2c<L, EL><<<grid, kThreads, C::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int L, int EL>
+static cudaError_t c2r_LE(const C2RArgs& a, int nplanes, cudaStream_t s) {
+  using C = RowCfg<L, EL>;
+  const dim3 grid((a.M + C::TEAMS - 1) / C::TEAMS, nplanes);
+  cudaError_t e = set_smem(k_rows_c2r<L, EL>, C::SMEM);
+  if (e != cudaSuccess) return e;
+  k_rows_c2r<L, EL><<<grid, kThreads, C::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int L>
-static cudaError_t c2r_L(const C2RArgs& a, int nplanes, cudaStream_t s) {
-  if (pair_rows_on(L)) return c2r_pair_L<L>(a, nplanes, s);
-  const dim3 grid((a.M + RowCfg<L>::TEAMS - 1) / RowCfg<L>::TEAMS, nplanes);
-  cudaError_t e = set_smem(k_rows_c2r<L>, RowCfg<L>::SMEM);
-  if (e != cudaSuccess) return e;
-  k_rows_c2r<L><<<grid, kThreads, RowCfg<L>::SMEM, s>>>(a);
-  return cudaGetLastError();
+static cudaError_t r2c_L(const R2CArgs& a, int nplanes, cudaStream_t s, int variant) {
+  if (!row_variant_ok(L, variant, false)) return cudaErrorInvalidValue;
+  if constexpr (L == 1024 || L == 2048) {
+    if (variant == 2) return r2c_LE<L, 32>(a, nplanes, s);
+  }
+  return r2c_LE<L, row_E(L)>(a, nplanes, s);
+}
+
+template <int L>
+static cudaError_t c2r_L(const C2RArgs& a, int nplanes, cudaStream_t s, int variant) {
+  if (!row_variant_ok(L, variant, true)) return cudaErrorInvalidValue;
+  if (variant == 1) return c2r_pair_L<L>(a, nplanes, s);
+  if constexpr (L == 1024 || L == 2048) {
+    if (variant == 2) return c2r_LE<L, 32>(a, nplanes, s);
+  }
+  return c2r_LE<L, row_E(L)>(a, nplanes, s);
 }
 
 // Row line length L = N/2 for N = 8 .. 4096.
@@ -91,14 +113,14 @@ static cudaError_t c2r_L(const C2RArgs& a, int nplanes, cudaStream_t s) {
     default: return cudaErrorInvalidValue; \
   }
 
-cudaError_t launch_rows_r2c(int L, const R2CArgs& a, int nplanes, cudaStream_t s) {
-#define CALL_(LL) r2c_L<LL>(a, nplanes, s)
+cudaError_t launch_rows_r2c(int L, const R2CArgs& a, int nplanes, cudaStream_t s, int variant) {
+#define CALL_(LL) r2c_L<LL>(a, nplanes, s, variant)
   FFST_DISPATCH_ROW(L, CALL_)
 #undef CALL_
 }
 
-cudaError_t launch_rows_c2r(int L, const C2RArgs& a, int nplanes, cudaStream_t s) {
-#define CALL_(LL) c2r_L<LL>(a, nplanes, s)
+cudaError_t launch_rows_c2r(int L, const C2RArgs& a, int nplanes, cudaStream_t s, int variant) {
+#define CALL_(LL) c2r_L<LL>(a, nplanes, s, variant)
   FFST_DISPATCH_ROW(L, CALL_)
 #undef CALL_
 }
