@@ -396,6 +396,17 @@ ffst_status ffst_plan_check(ffst_plan_t plan, void* stream);
 typedef struct ffst_batch_s* ffst_batch_t;
 ffst_status ffst_plan_batched(int n, const int* rows, const int* cols, const int* scales, int lanes,
                               ffst_batch_t* out);
+/*
+ * Autotune a batch: ffst_plan_autotune once per distinct image shape (on one
+ * of its plans), then that shape's configuration on every plan of the shape.
+ * Synchronises the device and allocates temporaries of the largest shape.
+ * storage and reps as for ffst_plan_autotune; stops at the first plan whose
+ * tuning fails and returns that status (plans tuned before it keep their
+ * new configuration).  Plans take a cached configuration of their shape at
+ * creation already; this call times again and appends to the cache.
+ */
+ffst_status ffst_batch_autotune(ffst_batch_t batch, int storage, int reps);
+
 /* Image i's size, scales, planes and lane.  Any output may be NULL. */
 ffst_status ffst_batch_info(ffst_batch_t batch, int i, int* rows, int* cols, int* scales, int* num_planes, int* lane);
 ffst_status ffst_forward_batched(ffst_batch_t batch, const float* const* imgs, void* const* coeffs, int storage,

@@ -420,6 +420,13 @@ class BatchPlan:
     def lanes(self):
         return [x[4] for x in self.info]
 
+    def autotune(self, dtype=None, reps: int = 3):
+        """Tune every distinct image shape once and use its configuration on all
+        plans of that shape (ffst_batch_autotune)."""
+        torch = _torch()
+        with torch.cuda.device(self.device):
+            _lib.ffst_batch_autotune(self.handle, _storage_of(dtype or torch.float32), reps)
+
     def close(self):
         if getattr(self, "handle", None):
             ffst_batch_destroy(self.handle)

@@ -66,6 +66,7 @@ SIGNATURES = [
     ("ffst_forward_batched", _I, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), _VP]),
     ("ffst_inverse_batched", _I, [_VP, ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     ("ffst_batch_destroy", None, [_VP]),
+    ("ffst_batch_autotune", _I, [_VP, _I, _I]),
     ("ffst_graph_capture_batched", _I, [_VP, _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I,
                                         ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     ("ffst_graph_launch", _I, [_VP, _VP]),
@@ -321,6 +322,10 @@ def ffst_inverse_batched(batch: int, coeffs, storage: int, plane_scales, imgs, s
 def ffst_batch_destroy(batch: int):
     if batch:
         lib().ffst_batch_destroy(batch)
+
+
+def ffst_batch_autotune(batch: int, storage: int = FFST_STORE_F32, reps: int = 3):
+    _check("ffst_batch_autotune", lib().ffst_batch_autotune(batch, int(storage), int(reps)))
 
 
 def ffst_graph_capture_batched(batch: int, what: int, imgs, coeffs, storage: int, plane_scales, out_imgs) -> int:

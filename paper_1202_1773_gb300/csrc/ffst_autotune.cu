@@ -9,7 +9,7 @@
 // variants: 16 elements per thread with radix 16 x 16 x 4 at length 1024,
 // two rows per team in packed FP32 pairs, or 32 elements per thread with
 // radix 32 x 32 and one exchange); for the inverse also the number of plane
-// chunks of its sum.  Every candidate is timed on the plan's own shape, the
+// chunks of its sum (1, 2, 4, 8, 16 or the plan's default).  Every candidate is timed on the plan's own shape, the
 // forward and the inverse apart, and the fastest kept.  With
 // FFST_AUTOTUNE_CACHE set, results are appended to that text file, one line
 // "<device> <rows> <cols> <scales> <storage> <forward MB> <inverse MB>
@@ -202,7 +202,7 @@ extern "C" ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int rep
   p->fuse_fwd = bf.fuse;
   p->row_fwd = bf.row;
   std::vector<int> splits = {p->inv_split_default};
-  for (int n : {1, 2, 4})
+  for (int n : {1, 2, 4, 8, 16})
     if (n != p->inv_split_default) splits.push_back(n);
   std::vector<Cand> ic;
   for (int n : splits) {
@@ -234,6 +234,22 @@ extern "C" ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int rep
   if (inv_mb) *inv_mb = best_i;
   return FFST_OK;
 }
+
+namespace ffst {
+
+// Give plan q the launch configuration of plan p (same shape).
+ffst_status copy_tuning(const ffst_plan_s* p, ffst_plan_s* q) {
+  if (p == q) return FFST_OK;
+  ffst_status st = plan_regroup(q, p->group_mb, p->group_mb_inv);
+  if (st != FFST_OK) return st;
+  q->fuse_fwd = p->fuse_fwd;
+  q->fuse_inv = p->fuse_inv;
+  q->row_fwd = p->row_fwd;
+  q->row_inv = p->row_inv;
+  return plan_set_inv_split(q, p->inv_split);
+}
+
+}  // namespace ffst
 
 extern "C" ffst_status ffst_plan_group_mb(ffst_plan_t plan, double* fwd_mb, double* inv_mb) {
   if (!plan || !fwd_mb || !inv_mb) return fail(FFST_ERR_INVALID_ARG, "ffst_plan_group_mb: NULL argument");

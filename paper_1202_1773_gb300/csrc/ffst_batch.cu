@@ -103,6 +103,31 @@ extern "C" ffst_status ffst_plan_batched(int n, const int* rows, const int* cols
   return FFST_OK;
 }
 
+extern "C" ffst_status ffst_batch_autotune(ffst_batch_t b, int storage, int reps) {
+  if (!b) return fail(FFST_ERR_INVALID_ARG, "ffst_batch_autotune: batch is NULL");
+  // one tuning run per distinct shape, then its configuration on every plan of that shape
+  std::vector<int> tuned(b->plans.size(), -1);  // plan index -> index of the tuned plan of its shape
+  for (int i = 0; i < b->n; ++i) {
+    const int pi = b->plan_of[i];
+    if (tuned[pi] >= 0) continue;
+    int src = -1;
+    for (size_t q = 0; q < b->plans.size() && src < 0; ++q)
+      if (tuned[q] == (int)q && b->plans[q]->M == b->rows[i] && b->plans[q]->N == b->cols[i] &&
+          b->plans[q]->j0 == b->scales[i])
+        src = (int)q;
+    if (src < 0) {
+      const ffst_status st = ffst_plan_autotune(b->plans[pi], storage, reps, nullptr, nullptr);
+      if (st != FFST_OK) return st;
+      tuned[pi] = pi;
+    } else {
+      const ffst_status st = copy_tuning(b->plans[src], b->plans[pi]);
+      if (st != FFST_OK) return st;
+      tuned[pi] = src;
+    }
+  }
+  return FFST_OK;
+}
+
 extern "C" ffst_status ffst_batch_info(ffst_batch_t b, int i, int* rows, int* cols, int* scales, int* num_planes,
                                        int* lane) {
   if (!b) return fail(FFST_ERR_INVALID_ARG, "ffst_batch_info: batch is NULL");

@@ -353,6 +353,8 @@ bool autotune_lookup(const ffst_plan_s* p, int storage, TuneConfig* cfg);
 bool row_variant_ok(int L, int variant, bool c2r);
 // fused plane-pass launches exist for this shape (ffst_fused.cu)
 bool fused_supported(int M, int N);
+// give plan q the launch configuration (budgets, kernels, plane chunks) of plan p of the same shape
+ffst_status copy_tuning(const ffst_plan_s* p, ffst_plan_s* q);
 
 // timing helpers
 void timer_begin(ffst_plan_s* p, int kind, cudaStream_t s, double bytes, cudaEvent_t* out_b);

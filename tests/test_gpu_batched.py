@@ -158,3 +158,28 @@ def test_full_256_image_batch_against_oracle(ffst):
     assert len(seen) == len(SIZES)
     g.close()
     bp.close()
+
+
+def test_batch_autotune_keeps_results(ffst):
+    # tuning a batch picks a configuration per distinct shape; the results
+    # stay those of the single plans to FP32 rounding (row variants and
+    # plane chunks reorder sums) and graph replay still equals eager runs
+    shapes, imgs = _batch(10, seed=4)
+    bp = ffst.BatchPlan(shapes, lanes=3)
+    bp.autotune(reps=1)
+    stacks = bp.forward(imgs)
+    recs = bp.inverse(stacks)
+    torch.cuda.synchronize()
+    for i, (r, c) in enumerate(shapes):
+        ref = ffst.Plan(r, c).forward(imgs[i])
+        assert float(torch.linalg.norm(stacks[i] - ref) / torch.linalg.norm(ref)) <= 1e-6, i
+        assert float(torch.linalg.norm(recs[i] - imgs[i]) / torch.linalg.norm(imgs[i])) <= 1e-5, i
+    outs = [torch.empty_like(x) for x in imgs]
+    g_stacks = bp.empty_stacks()
+    g = bp.capture(imgs, g_stacks, outs, what=3)
+    g.launch()
+    torch.cuda.synchronize()
+    for i in range(len(shapes)):
+        assert torch.equal(g_stacks[i], stacks[i]) and torch.equal(outs[i], recs[i]), i
+    g.close()
+    bp.close()
