@@ -84,12 +84,17 @@ __device__ __forceinline__ void dft(float2 (&x)[R]) {
   } else if constexpr (R == 4) {
     const float2 t0 = cadd(x[0], x[2]), t1 = csub(x[0], x[2]);
     const float2 t2 = cadd(x[1], x[3]), t3 = csub(x[1], x[3]);
-    // (-i) t3 forward, (+i) t3 inverse
-    const float2 r3 = INV ? make_float2(-t3.y, t3.x) : make_float2(t3.y, -t3.x);
     x[0] = cadd(t0, t2);
     x[2] = csub(t0, t2);
-    x[1] = cadd(t1, r3);
-    x[3] = csub(t1, r3);
+    // t1 -/+ i t3 (forward / inverse), componentwise: the swapped pair never
+    // has to be formed
+    if constexpr (INV) {
+      x[1] = make_float2(t1.x - t3.y, t1.y + t3.x);
+      x[3] = make_float2(t1.x + t3.y, t1.y - t3.x);
+    } else {
+      x[1] = make_float2(t1.x + t3.y, t1.y - t3.x);
+      x[3] = make_float2(t1.x - t3.y, t1.y + t3.x);
+    }
   } else {
     constexpr int R1 = (R == 8) ? 2 : ((R == 16 || R == 32) ? 4 : 8);
     constexpr int R2 = R / R1;
