@@ -693,7 +693,7 @@ def run_forms(plan, pool, stack, rec, plain_value, args, dev):
     for (r, c) in sorted(set(shapes)):
         srcs[(r, c)] = [torch.from_numpy(inputs.scaled_cartoon(r, c, seed=300 + q)).to(dev) for q in range(2)]
     imgs = [srcs[sh][i % 2] for i, sh in enumerate(shapes)]
-    bp = ffst.BatchPlan(shapes, lanes=4, device=dev)
+    bp = ffst.BatchPlan(shapes, lanes=8, device=dev)
     stacks = bp.empty_stacks()
     outs = [torch.empty(sh, device=dev) for sh in shapes]
     graph = bp.capture(imgs, stacks, outs, what=3)
@@ -701,10 +701,26 @@ def run_forms(plan, pool, stack, rec, plain_value, args, dev):
     ms = _time_steps(lambda q: graph.launch(), max(2, args.steps // 5), dev)
     errs = [float(torch.linalg.norm(outs[i] - imgs[i]) / torch.linalg.norm(imgs[i])) for i in range(n)]
     byts = 2.0 * total * 4 + 8.0 * sum(r * c for r, c in shapes)
+    # the same 256 round trips one after another through single plans (one
+    # per shape, eager launches on one stream): what the batch saves
+    singles = {sh: ffst.Plan(*sh, device=dev) for sh in sorted(set(shapes))}
+    s_stk = {sh: torch.empty(singles[sh].shape, device=dev) for sh in singles}
+    s_rec = {sh: torch.empty(sh, device=dev) for sh in singles}
+
+    def _sequential(q):
+        for i, sh in enumerate(shapes):
+            singles[sh].forward(imgs[i], out=s_stk[sh])
+            singles[sh].inverse(s_stk[sh], out=s_rec[sh])
+
+    seq_ms = _time_steps(_sequential, 2, dev)
+    for p_ in singles.values():
+        p_.close()
+    del s_stk, s_rec
     out["batched"] = {"value": total / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-                      "vs_plain": total / (ms / 1e3) / plain_value, "images": n,
+                      "vs_plain": total / (ms / 1e3) / plain_value,
+                      "sequential_single_plans_ms": seq_ms, "vs_sequential": seq_ms / ms, "images": n,
                       "sizes": {f"{r}x{c}": shapes.count((r, c)) for (r, c) in sorted(set(shapes))},
-                      "coeffs_per_step": total, "lanes": 4, "graph": True,
+                      "coeffs_per_step": total, "lanes": 8, "graph": True,
                       "roofline_step_frac": byts / (ms / 1e3) / 1e9 / _peaks()[0],
                       "accuracy": {"reconstruction_rel_l2_max": max(errs)}}
     graph.close()

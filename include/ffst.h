@@ -276,7 +276,10 @@ ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int reps, double* 
  *                       with packed two-lane FP32 arithmetic (forward only,
  *                       power-of-two widths 512..4096); 2 = 32 elements per
  *                       thread (radix 32 x 32, one exchange; widths 2048 and
- *                       4096).  Fused launches use 0.
+ *                       4096); 3 = as 2 with the exchange done by warp
+ *                       shuffles instead of shared memory (width 2048 only:
+ *                       one warp per 1024-point line; results bitwise those
+ *                       of 2).  Fused launches use 0.
  * The same transform in every configuration (the row variants differ in
  * rounding only).  FFST_ERR_INVALID_ARG for flags other than 0/1 or a row
  * variant the plan's width does not have.

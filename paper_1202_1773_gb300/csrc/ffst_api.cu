@@ -97,7 +97,7 @@ static int inv_row_variant(const ffst_plan_s* p) {
   return use_fused(p) || use_sched(p) || p->bl_rows.n ? 0 : p->row_inv;
 }
 static const float2* row_table(const ffst_plan_s* p, int variant) {
-  return variant == 2 ? p->d_tw_rows32 : p->d_tw_rows;
+  return variant >= 2 ? p->d_tw_rows32 : p->d_tw_rows;  // 2 and 3: the (L, 32) pass table
 }
 
 static Group all_planes(const ffst_plan_s* p) { return Group{p->pr0, p->pr1, 0, 0, p->total_items}; }

@@ -186,7 +186,7 @@ extern "C" ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int rep
   };
   std::vector<Cand> fc;
   if (fusable) fc.push_back({1, 0, 0});
-  for (int v = 0; v <= 2; ++v)
+  for (int v = 0; v <= kRowVariants - 1; ++v)
     if (v == 0 || (native && row_variant_ok(L, v, true))) fc.push_back({0, v, 0});
   Cand bf = {p->fuse_fwd, p->row_fwd, 0};
   float tb = 1e30f;
@@ -207,7 +207,7 @@ extern "C" ffst_status ffst_plan_autotune(ffst_plan_t plan, int storage, int rep
   std::vector<Cand> ic;
   for (int n : splits) {
     if (fusable) ic.push_back({1, 0, n});
-    for (int v = 0; v <= 2; ++v)
+    for (int v = 0; v <= kRowVariants - 1; ++v)
       if (v == 0 || (native && row_variant_ok(L, v, false))) ic.push_back({0, v, n});
   }
   Cand bi = {p->fuse_inv, p->row_inv, p->inv_split};

@@ -253,6 +253,60 @@ __device__ __forceinline__ void stockham(float2 (&v)[E], float2* buf, int t, con
   }
 }
 
+// Register array of one lane rotated left by a lane-dependent amount s in
+// [0, 32): u[i] <- u[(i + s) mod 32], as five conditional rotations by
+// 1, 2, 4, 8, 16 (selects on the bits of s; no local memory).
+__device__ __forceinline__ void rotate_regs32(float2 (&u)[32], int s) {
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    const bool on = (s >> b) & 1;
+    constexpr int kHead = 16;
+    const int d = 1 << b;
+    float2 head[kHead];  // u[0, d) before it is overwritten
+#pragma unroll
+    for (int i = 0; i < kHead; ++i)
+      if (i < d) head[i] = u[i];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const float2 src = (i + d < 32) ? u[i + d] : head[(i + d - 32) % kHead];
+      u[i] = on ? src : u[i];
+    }
+  }
+}
+
+// Transpose of a warp's 32 x 32 register tile by warp shuffles: register r
+// of lane l moves to register l of lane r.  Lane l first rotates its
+// registers by l, so that shuffle k can take the same register k from every
+// lane (source lane l - k delivers its element for lane l); the received
+// elements arrive in the order of their source lanes reversed and rotated by
+// l, which the second rotation undoes.  64 shuffles and about 640 selects
+// per lane, against 32 stores and 32 loads through shared memory.
+__device__ __forceinline__ void warp_transpose32(float2 (&v)[32], int lane) {
+  rotate_regs32(v, lane);  // v[i] = a[lane][(i + lane) mod 32]
+  float2 z[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int src = (lane - i) & 31;  // src's register i holds a[src][lane]
+    z[(32 - i) & 31] = make_float2(__shfl_sync(0xffffffffu, v[i].x, src), __shfl_sync(0xffffffffu, v[i].y, src));
+  }
+  // z[j] = a[(lane + j) mod 32][lane]; wanted v[s] = a[s][lane] = z[(s - lane) mod 32]
+  rotate_regs32(z, (32 - lane) & 31);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = z[i];
+}
+
+// A 1024-point line run by one warp with 32 elements per lane (the layout
+// contract above with T = E = 32) whose one exchange is warp_transpose32
+// instead of shared memory: the same two radix-32 passes, twiddles and
+// results as stockham<1024, 32>.
+template <bool INV>
+__device__ __forceinline__ void line_fft_shfl1024(float2 (&v)[32], int t, const float2* __restrict__ tw) {
+  dft<32, INV>(v);                               // pass 1 (Ns = 1): y[32 t + r] = v[r]
+  warp_transpose32(v, t);                        // v[r] = y[t + 32 r]
+  pass_twiddles<32, INV>(v, tw + 31 + t, 32);    // pass 2 (Ns = 32, kk = t)
+  dft<32, INV>(v);                               // v[r] = X[t + 32 r]
+}
+
 // Mixed-radix lines (L not a power of two): the same Stockham passes, with
 // the data in shared memory between all passes (ping-pong between buf[0, L)
 // and buf[L, 2L)); NT threads share each pass's butterflies.

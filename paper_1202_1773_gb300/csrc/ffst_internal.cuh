@@ -373,6 +373,7 @@ struct TuneConfig {
 bool autotune_lookup(const ffst_plan_s* p, int storage, TuneConfig* cfg);
 // row kernel variant v (ffst_rows.cu) exists for half-length L
 bool row_variant_ok(int L, int variant, bool c2r);
+constexpr int kRowVariants = 4;  // row-FFT variants 0..3 (ffst_rows.cu)
 // fused plane-pass launches exist for this shape (ffst_fused.cu)
 bool fused_supported(int M, int N);
 // give plan q the launch configuration (budgets, kernels, plane chunks) of plan p of the same shape

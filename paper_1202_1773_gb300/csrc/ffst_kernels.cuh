@@ -158,9 +158,10 @@ struct R2CArgs {
   int* err;                  // plan error word (FFST_CHECK builds)
 };
 
-template <int L, int EL = row_E(L)>
+template <int L, int EL = row_E(L), bool XSHFL = false>
 __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, float2* smem) {
   using C = RowCfg<L, EL>;
+  static_assert(!XSHFL || (L == 1024 && EL == 32), "the shuffle exchange is built for 1024-point lines of one warp");
   constexpr int E = C::E, T = C::T, N = 2 * L;
   const int team = threadIdx.x / T, t = threadIdx.x % T;
   float2* buf = smem + team * C::BUF;
@@ -192,7 +193,8 @@ __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, 
       v[m] = make_float2(x.x * us, x.y * us);
     }
   }
-  line_fft<L, E, false, C::SYNC>(v, buf, t, a.tw, 1 + team);
+  if constexpr (XSHFL) line_fft_shfl1024<false>(v, t, a.tw);
+  else line_fft<L, E, false, C::SYNC>(v, buf, t, a.tw, 1 + team);
   team_store<E, T>(buf, t, v);
   team_sync<C::SYNC, T>(1 + team);
   if (!act) return;
@@ -268,9 +270,10 @@ __device__ __forceinline__ float plane_scale_of(const float* partials, int item0
 // `ps` is the plane factor s_i multiplied into the output (c2r_plane_factor).
 // The statistics partials always cover RowCfg<L>::TEAMS rows (the default
 // geometry), so a block of another geometry writes TEAMS / that of them.
-template <int L, int EL = row_E(L)>
+template <int L, int EL = row_E(L), bool XSHFL = false>
 __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, float2* smem, float ps) {
   using C = RowCfg<L, EL>;
+  static_assert(!XSHFL || (L == 1024 && EL == 32), "the shuffle exchange is built for 1024-point lines of one warp");
   constexpr int E = C::E, T = C::T, N = 2 * L;
   const int team = threadIdx.x / T, t = threadIdx.x % T;
   float2* buf = smem + team * C::BUF;
@@ -315,7 +318,8 @@ __device__ __forceinline__ void rows_c2r_body(const C2RArgs& a, int bx, int by, 
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = make_float2(v[m].x * s, v[m].y * s);
   }
-  line_fft<L, E, true, C::SYNC>(v, buf, t, a.tw, 1 + team);
+  if constexpr (XSHFL) line_fft_shfl1024<true>(v, t, a.tw);
+  else line_fft<L, E, true, C::SYNC>(v, buf, t, a.tw, 1 + team);
   if (a.shrink || a.abs_partials) {  // uniform over the launch
     // v holds c * ps: threshold and statistics act on c (ps is a power of two)
     __shared__ float red[kThreads / 32];

@@ -1,8 +1,10 @@
 // Plan construction: FP64 host tables, plane indexing, spectral supports,
 // plane grouping and workspace; plus the spectra export kernel.
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
@@ -521,9 +523,39 @@ extern "C" ffst_status ffst_plan(int rows, int cols, int scales, ffst_plan_t* ou
                       FFST_SPACING_COMMON, out);
 }
 
+// FFST_PLAN_TIMES=1: wall time of each phase of plan creation on stderr
+// (the device is synchronised at every mark, so the marks add a little).
+namespace {
+struct PhaseTimer {
+  bool on = false;
+  std::chrono::steady_clock::time_point t0, last;
+  std::string line;
+  PhaseTimer() {
+    const char* e = std::getenv("FFST_PLAN_TIMES");
+    on = e && e[0] == '1';
+    t0 = last = std::chrono::steady_clock::now();
+  }
+  void mark(const char* what) {
+    if (!on) return;
+    cudaDeviceSynchronize();
+    const auto now = std::chrono::steady_clock::now();
+    char b[96];
+    std::snprintf(b, sizeof b, " %s %.3f", what, std::chrono::duration<double, std::milli>(now - last).count());
+    line += b;
+    last = now;
+  }
+  ~PhaseTimer() {
+    if (on)
+      std::fprintf(stderr, "ffst_plan ms:%s | total %.3f\n", line.c_str(),
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+  }
+};
+}  // namespace
+
 extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant, int vfun, int vorder, int max_scale,
                                     int spacing, ffst_plan_t* out) {
   if (!out) return fail(FFST_ERR_INVALID_ARG, "ffst_plan: out is NULL");
+  PhaseTimer ptime;
   *out = nullptr;
   if (variant != FFST_VARIANT_CLASSIC && variant != FFST_VARIANT_SMOOTH)
     return fail(FFST_ERR_INVALID_ARG, "ffst_plan_ex: variant must be FFST_VARIANT_CLASSIC or FFST_VARIANT_SMOOTH");
@@ -650,6 +682,7 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
   p->win.sig_row = p->win.sig_col + (size_t)j0 * ncol;
   p->win.alp_col = p->win.sig_row + (size_t)j0 * nrow;
   p->win.alp_row = p->win.alp_col + (size_t)j0 * ncol;
+  ptime.mark("tables");
 
   // twiddles (FP64 -> FP32): row lines of length N/2, their real split, column lines of length M
   if (nat_rows) {
@@ -694,6 +727,7 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
     }
   }
   p->P = nat_cols ? cols_per_cta(rows) : blue_lines_per_block(p->bl_cols.L2);
+  ptime.mark("twiddles");
 
   // supports
   if ((e = cudaMalloc(&p->d_planes, p->planes.size() * sizeof(PlaneDesc))) != cudaSuccess)
@@ -733,6 +767,7 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
     e = launch_ranges(p.get(), 0);
     if (e != cudaSuccess) return cuda_fail(e, "ffst_plan row ranges");
   }
+  ptime.mark("support+ranges");
 
   // kernel configuration and groups (autotune cache, else FFST_GROUP_MB* and defaults)
   TuneConfig tc;
@@ -752,6 +787,7 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
       if (f[0] == '0') p->fuse_fwd = p->fuse_inv = 0;
     if (const char* f = std::getenv("FFST_FUSE_FWD")) p->fuse_fwd = f[0] == '0' ? 0 : 1;
   }
+  ptime.mark("groups");
 
   // workspace
   const size_t spec = (size_t)rows * p->Hc;
@@ -769,15 +805,18 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
     if ((e = cudaMalloc(&p->d_abs_partials, sizeof(float) * (size_t)p->eta * p->row_blocks)) != cudaSuccess)
       return cuda_fail(e, "statistics partials");
   }
+  ptime.mark("workspace");
   {
     p->inv_split_default = default_inv_split(p.get());
     const int ns = (tuned && tc.inv_split >= 1 && tc.inv_split <= kMaxInvSplit) ? tc.inv_split : p->inv_split_default;
     const ffst_status st = plan_set_inv_split(p.get(), ns);
     if (st != FFST_OK) return st;
   }
+  ptime.mark("accumulators");
   if ((e = cudaMalloc(&p->d_invD, spec * sizeof(float))) != cudaSuccess) return cuda_fail(e, "normalisation");
   if ((e = launch_inv_norm(p.get(), 0)) != cudaSuccess) return cuda_fail(e, "ffst_plan normalisation");
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "ffst_plan");
+  ptime.mark("normalisation");
   *out = p.release();
   return FFST_OK;
 }

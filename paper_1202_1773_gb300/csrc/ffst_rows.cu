@@ -7,7 +7,10 @@
 //  1  paired rows (C2R only): two rows per team in packed FP32 pairs,
 //     power-of-two L in 256..2048 (ffst_rows_pair.cuh);
 //  2  32 elements per thread, L = 1024 and 2048 (radix 32 x 32 at L = 1024:
-//     one warp per line and one shared-memory exchange; budget of 3 blocks).
+//     one warp per line and one shared-memory exchange; budget of 3 blocks);
+//  3  as 2 at L = 1024, with the exchange done by warp shuffles
+//     (warp_transpose32; bitwise the results of 2; budget of 2 blocks for
+//     the 32 extra registers of the transpose).
 // Every variant computes the same transform; only the operation order of
 // the FFT (and with it the rounding) differs.
 #include "ffst_rows_pair.cuh"
@@ -18,6 +21,7 @@ bool row_variant_ok(int L, int variant, bool c2r) {
   if (variant == 0) return true;
   if (variant == 1) return c2r && is_pow2c(L) && L >= 256 && L <= 2048;
   if (variant == 2) return L == 1024 || L == 2048;
+  if (variant == 3) return L == 1024;
   return false;
 }
 
@@ -40,35 +44,40 @@ static cudaError_t c2r_pair_L(const C2RArgs& a, int nplanes, cudaStream_t s) {
   }
 }
 
-template <int L, int EL>
-__global__ void __launch_bounds__(kThreads, EL >= 32 ? 3 : FFST_MIN_BLOCKS) k_rows_r2c(R2CArgs a) {
-  extern __shared__ __align__(128) float2 smem[];
-  rows_r2c_body<L, EL>(a, blockIdx.x, blockIdx.y, smem);
+template <int EL, bool XSHFL>
+constexpr int row_min_blocks() {
+  return XSHFL ? 2 : (EL >= 32 ? 3 : FFST_MIN_BLOCKS);
 }
 
-template <int L, int EL>
-__global__ void __launch_bounds__(kThreads, EL >= 32 ? 3 : FFST_MIN_BLOCKS) k_rows_c2r(C2RArgs a) {
+template <int L, int EL, bool XSHFL = false>
+__global__ void __launch_bounds__(kThreads, row_min_blocks<EL, XSHFL>()) k_rows_r2c(R2CArgs a) {
   extern __shared__ __align__(128) float2 smem[];
-  rows_c2r_body<L, EL>(a, blockIdx.x, blockIdx.y, smem, c2r_plane_factor(a, blockIdx.y));
+  rows_r2c_body<L, EL, XSHFL>(a, blockIdx.x, blockIdx.y, smem);
 }
 
-template <int L, int EL>
+template <int L, int EL, bool XSHFL = false>
+__global__ void __launch_bounds__(kThreads, row_min_blocks<EL, XSHFL>()) k_rows_c2r(C2RArgs a) {
+  extern __shared__ __align__(128) float2 smem[];
+  rows_c2r_body<L, EL, XSHFL>(a, blockIdx.x, blockIdx.y, smem, c2r_plane_factor(a, blockIdx.y));
+}
+
+template <int L, int EL, bool XSHFL = false>
 static cudaError_t r2c_LE(const R2CArgs& a, int nplanes, cudaStream_t s) {
   using C = RowCfg<L, EL>;
   const dim3 grid((a.M + C::TEAMS - 1) / C::TEAMS, nplanes);
-  cudaError_t e = set_smem(k_rows_r2c<L, EL>, C::SMEM);
+  cudaError_t e = set_smem(k_rows_r2c<L, EL, XSHFL>, C::SMEM);
   if (e != cudaSuccess) return e;
-  k_rows_r2c<L, EL><<<grid, kThreads, C::SMEM, s>>>(a);
+  k_rows_r2c<L, EL, XSHFL><<<grid, kThreads, C::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int L, int EL>
+template <int L, int EL, bool XSHFL = false>
 static cudaError_t c2r_LE(const C2RArgs& a, int nplanes, cudaStream_t s) {
   using C = RowCfg<L, EL>;
   const dim3 grid((a.M + C::TEAMS - 1) / C::TEAMS, nplanes);
-  cudaError_t e = set_smem(k_rows_c2r<L, EL>, C::SMEM);
+  cudaError_t e = set_smem(k_rows_c2r<L, EL, XSHFL>, C::SMEM);
   if (e != cudaSuccess) return e;
-  k_rows_c2r<L, EL><<<grid, kThreads, C::SMEM, s>>>(a);
+  k_rows_c2r<L, EL, XSHFL><<<grid, kThreads, C::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -77,6 +86,9 @@ static cudaError_t r2c_L(const R2CArgs& a, int nplanes, cudaStream_t s, int vari
   if (!row_variant_ok(L, variant, false)) return cudaErrorInvalidValue;
   if constexpr (L == 1024 || L == 2048) {
     if (variant == 2) return r2c_LE<L, 32>(a, nplanes, s);
+  }
+  if constexpr (L == 1024) {
+    if (variant == 3) return r2c_LE<L, 32, true>(a, nplanes, s);
   }
   return r2c_LE<L, row_E(L)>(a, nplanes, s);
 }
@@ -87,6 +99,9 @@ static cudaError_t c2r_L(const C2RArgs& a, int nplanes, cudaStream_t s, int vari
   if (variant == 1) return c2r_pair_L<L>(a, nplanes, s);
   if constexpr (L == 1024 || L == 2048) {
     if (variant == 2) return c2r_LE<L, 32>(a, nplanes, s);
+  }
+  if constexpr (L == 1024) {
+    if (variant == 3) return c2r_LE<L, 32, true>(a, nplanes, s);
   }
   return c2r_LE<L, row_E(L)>(a, nplanes, s);
 }
