@@ -49,6 +49,12 @@ int blue_lines_per_block(int L2);
 
 // Host tables of a line of length n (FP64, rounded to FP32).
 void blue_tables(int n, int* L2, std::vector<float2>* chirp, std::vector<float2>* bhat);
+// Lengths with no prime factor above 7: the radices of the mixed-radix
+// passes (8s, then a 4 or 2, then 3s, 5s, 7s) packed 4 bits per pass, and
+// the pass twiddle table (n - 1 entries).  False for other lengths.
+bool smooth_line(int n, int* nrad, unsigned long long* radices, std::vector<float2>* tw);
+// The power of two >= 2n - 1 (line geometry of the generic kernels).
+int blue_L2(int n);
 
 cudaError_t launch_blue_rows_r2c(const BlueLine& b, const R2CArgs& a, int nplanes, cudaStream_t s);
 cudaError_t launch_blue_rows_c2r(const BlueLine& b, const C2RArgs& a, int nplanes, cudaStream_t s);
@@ -82,14 +88,90 @@ __device__ __forceinline__ bool in_cyclic(int r, int2 rg, int n) {
   return q < rg.y;
 }
 
+// One Stockham pass of radix R over a line of length n in shared memory
+// (the autosort of ffst_fft.cuh with a runtime length): butterfly j < n/R
+// takes a[j + r n/R], applies W_{Ns R}^{(j mod Ns) r} and the R-point DFT,
+// and writes c[(j - j mod Ns) R + j mod Ns + r Ns].  Team threads t, t + T,
+// ... share the butterflies.
+template <int R, bool INV>
+__device__ __forceinline__ void smooth_pass(const float2* a, float2* c, int n, int Ns, const float2* __restrict__ tw,
+                                            int t, int T) {
+  const int nb = n / R;
+  for (int j = t; j < nb; j += T) {
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = a[j + r * nb];
+    const int kk = j % Ns;
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = __ldg(&tw[(Ns - 1) + (r - 1) * Ns + kk]);
+        if (INV) w.y = -w.y;
+        x[r] = cmul(x[r], w);
+      }
+    }
+    dft<R, INV>(x);
+    float2* dst = c + (j - kk) * R + kk;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[r * Ns] = x[r];
+  }
+}
+
+// DFT (INV: unnormalised inverse) of length b.n, b.nrad > 0, of the line in
+// a[0, n) of a team's buffer, ping-ponging with c[0, n); returns the buffer
+// that holds the result.  Every thread of the block calls it: a barrier
+// follows each pass.  Not inlined: one copy serves every line geometry.
+template <bool INV>
+__device__ __noinline__ float2* smooth_dft(float2* a, float2* c, int n, int nrad, unsigned long long radices,
+                                           const float2* __restrict__ tw, int t, int T) {
+  int Ns = 1;
+  for (int s = 0; s < nrad; ++s) {
+    const int R = (int)((radices >> (4 * s)) & 15u);
+    switch (R) {
+      case 2: smooth_pass<2, INV>(a, c, n, Ns, tw, t, T); break;
+      case 3: smooth_pass<3, INV>(a, c, n, Ns, tw, t, T); break;
+      case 4: smooth_pass<4, INV>(a, c, n, Ns, tw, t, T); break;
+      case 5: smooth_pass<5, INV>(a, c, n, Ns, tw, t, T); break;
+      case 7: smooth_pass<7, INV>(a, c, n, Ns, tw, t, T); break;
+      default: smooth_pass<8, INV>(a, c, n, Ns, tw, t, T); break;
+    }
+    __syncthreads();
+    float2* x = a;
+    a = c;
+    c = x;
+    Ns *= R;
+  }
+  return a;
+}
+
 // DFT (INV: unnormalised inverse DFT) of length b.n of the line whose
 // element j = t + T m (j < b.n; the rest is ignored) thread t holds in v[m];
 // on return v[m] holds output k = t + T m (zero for k >= b.n).  Every thread
 // of the block calls it (block barriers); it ends with a barrier after its
-// last read of `buf`.
+// last read of `buf`.  Lengths with no prime factor above 7 run the
+// mixed-radix passes (buf holds 2n slots: L2 >= 2n); the others Bluestein's
+// convolution.
 template <int L2, bool INV>
 __device__ __forceinline__ void blue_dft(float2 (&v)[BlueCfg<L2>::E], float2* buf, int t, const BlueLine& b) {
   constexpr int E = BlueCfg<L2>::E, T = BlueCfg<L2>::T;
+  static_assert(BlueCfg<L2>::BUF >= L2, "a smooth line ping-pongs through 2n <= L2 buffer slots");
+  if (b.nrad > 0) {
+    __syncthreads();  // earlier reads of buf by other teams' threads are done
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int j = t + T * m;
+      if (j < b.n) buf[j] = v[m];
+    }
+    __syncthreads();
+    const float2* res = smooth_dft<INV>(buf, buf + b.n, b.n, b.nrad, b.radices, b.mtw, t, T);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = t + T * m;
+      v[m] = k < b.n ? res[k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    return;
+  }
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int j = t + T * m;

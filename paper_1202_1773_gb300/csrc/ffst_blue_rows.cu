@@ -10,9 +10,54 @@ namespace ffst {
 // ---------------------------------------------------------------------------
 // host tables
 // ---------------------------------------------------------------------------
-void blue_tables(int n, int* L2out, std::vector<float2>* chirp, std::vector<float2>* bhat) {
+int blue_L2(int n) {
   int L2 = kBlueMinL2;
   while (L2 < 2 * n - 1) L2 *= 2;
+  return L2;
+}
+
+bool smooth_line(int n, int* nrad, unsigned long long* radices, std::vector<float2>* tw) {
+  std::vector<int> rs;
+  int m = n;
+  while (m % 8 == 0) {
+    rs.push_back(8);
+    m /= 8;
+  }
+  if (m % 4 == 0) {
+    rs.push_back(4);
+    m /= 4;
+  } else if (m % 2 == 0) {
+    rs.push_back(2);
+    m /= 2;
+  }
+  for (int p : {3, 5, 7})
+    while (m % p == 0) {
+      rs.push_back(p);
+      m /= p;
+    }
+  if (m != 1 || rs.empty() || rs.size() > 16) return false;
+  *nrad = (int)rs.size();
+  *radices = 0;
+  for (size_t s = 0; s < rs.size(); ++s) *radices |= (unsigned long long)rs[s] << (4 * s);
+  // pass s (sub-transform length Ns, radix R): W_{Ns R}^{kk r} = exp(-2 pi i kk r / (Ns R))
+  // at (Ns - 1) + (r - 1) Ns + kk, the angle reduced exactly (kk r mod Ns R)
+  tw->assign(n > 1 ? n - 1 : 1, make_float2(1.f, 0.f));
+  const double pi = 3.14159265358979323846;
+  long long Ns = 1;
+  for (int R : rs) {
+    for (int r = 1; r < R; ++r)
+      for (long long kk = 0; kk < Ns; ++kk) {
+        const long long q = (kk * r) % (Ns * R);
+        const double ang = -2.0 * pi * (double)q / (double)(Ns * R);
+        (*tw)[(Ns - 1) + (r - 1) * Ns + kk] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+      }
+    Ns *= R;
+  }
+  return true;
+}
+
+void blue_tables(int n, int* L2out, std::vector<float2>* chirp, std::vector<float2>* bhat) {
+  const int L2 = blue_L2(n);
   *L2out = L2;
   const double pi = 3.14159265358979323846;
   // w_j = exp(-i pi j^2 / n): j^2 reduced mod 2n exactly, so the angle stays small

@@ -57,13 +57,14 @@ __device__ __forceinline__ float2 twiddle_c(float2 x) {
   }
 }
 
-// In-place R-point DFT of x (natural order in and out), R in {1,2,4,8,16,32,64}.
+// In-place R-point DFT of x (natural order in and out), R in {1,2,4,8,16,32,64}
+// and the odd radices 3, 5, 7.
 // R = R1*R2: R1 interleaved DFTs of length R2, twiddles W_R^{n1 k2}, then R2
 // DFTs of length R1 (X[k2 + R2 k1]).
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2 (&x)[R]) {
   if constexpr (R == 1) {
-  } else if constexpr (R == 3 || R == 5) {
+  } else if constexpr (R == 3 || R == 5 || R == 7) {
     // odd radices of mixed-radix lines: the DFT sum with constant roots
     float2 y[R];
     static_for<0, R>([&](auto kc) {

@@ -268,10 +268,15 @@ namespace ffst {
 // Tables of the generic-length lines of one dimension (ffst_blue.cuh).
 struct BlueLine {
   int n = 0;                      // line length; 0: the dimension runs native FFT lines
-  int L2 = 0;                     // convolution length, the power of two >= 2n - 1
+  int L2 = 0;                     // the power of two >= 2n - 1 (thread layout; Bluestein convolution length)
   const float2* chirp = nullptr;  // w_j = exp(-i pi j^2 / n), j < n (FP64-generated)
   const float2* bhat = nullptr;   // FFT_L2 of the filter conj(w_|m|), times 1/L2
   const float2* tw = nullptr;     // pass table (L2, blue_E(L2))
+  // n with no prime factor above 7: the DFT runs as mixed-radix Stockham
+  // passes in shared memory instead of Bluestein (nrad > 0)
+  int nrad = 0;                   // number of passes
+  unsigned long long radices = 0; // radix of pass s in bits [4s, 4s + 4): 2, 3, 4, 5, 7 or 8
+  const float2* mtw = nullptr;    // pass twiddles W_{Ns R}^{kk r} at (Ns - 1) + (r - 1) Ns + kk
 };
 
 struct Sched {

@@ -695,14 +695,27 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
   if (nat_cols) {
     if ((e = upload(&p->d_tw_cols, pass_table(rows, col_E(rows)))) != cudaSuccess) return cuda_fail(e, "twiddles");
   }
-  // generic lines: chirp | filter spectrum | pass table, per generic dimension
+  // generic lines, per generic dimension: mixed-radix pass table (lengths
+  // with no prime factor above 7), else chirp | filter spectrum | pass table
   {
     std::vector<float2> tab;
     size_t off[2][3] = {};
     const int lens[2] = {nat_rows ? 0 : cols, nat_cols ? 0 : rows};
     int L2s[2] = {0, 0};
+    int nrads[2] = {0, 0};
+    unsigned long long rcodes[2] = {0, 0};
+    // FFST_BLUESTEIN=1 keeps Bluestein lines for every generic length (A/B timing, tests)
+    const char* fb = std::getenv("FFST_BLUESTEIN");
+    const bool all_blue = fb && fb[0] == '1';
     for (int q = 0; q < 2; ++q) {
       if (!lens[q]) continue;
+      std::vector<float2> mtw;
+      if (!all_blue && smooth_line(lens[q], &nrads[q], &rcodes[q], &mtw)) {
+        L2s[q] = blue_L2(lens[q]);
+        off[q][0] = tab.size();
+        tab.insert(tab.end(), mtw.begin(), mtw.end());
+        continue;
+      }
       std::vector<float2> chirp, bhat;
       blue_tables(lens[q], &L2s[q], &chirp, &bhat);
       const std::vector<float2> tw = pass_table(L2s[q], blue_E(L2s[q]));
@@ -720,9 +733,15 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
         if (!lens[q]) continue;
         bl[q]->n = lens[q];
         bl[q]->L2 = L2s[q];
-        bl[q]->chirp = p->d_blue + off[q][0];
-        bl[q]->bhat = p->d_blue + off[q][1];
-        bl[q]->tw = p->d_blue + off[q][2];
+        if (nrads[q] > 0) {
+          bl[q]->nrad = nrads[q];
+          bl[q]->radices = rcodes[q];
+          bl[q]->mtw = p->d_blue + off[q][0];
+        } else {
+          bl[q]->chirp = p->d_blue + off[q][0];
+          bl[q]->bhat = p->d_blue + off[q][1];
+          bl[q]->tw = p->d_blue + off[q][2];
+        }
       }
     }
   }

@@ -1,9 +1,12 @@
 """Generic sizes (odd, prime, and lengths without a native FFT line) against
 the FP64 oracle.
 
-A dimension whose length has no native line runs Bluestein lines: the DFT of
-length n as a chirp convolution through power-of-two FFTs of length
-L2 >= 2n - 1.  Everything after the line transforms (the Sec. 3.1 forward,
+A dimension whose length has no native line runs generic lines: lengths
+with no prime factor above 7 as mixed-radix (2, 3, 4, 5, 7, 8) Stockham
+passes in shared memory, the others as Bluestein lines (the DFT of length n
+as a chirp convolution through power-of-two FFTs of length L2 >= 2n - 1;
+FFST_BLUESTEIN=1 at plan creation forces them for every length).
+Everything after the line transforms (the Sec. 3.1 forward,
 the Sec. 3.3 inverse and adjoint, low-precision storage, the fused
 statistics and shrinkage, the one-sided complex shearlets of Sec. 3.8.2,
 the plane chunks of the inverse) is the same code as at native sizes, so the
@@ -242,3 +245,51 @@ def test_batched_and_graph_at_generic_sizes(ffst):
         assert torch.equal(outs[i], recs[i]), i
     g.close()
     bp.close()
+
+
+@pytest.mark.parametrize("shape", [(100, 150), (63, 64), (240, 250), (98, 343), (36, 1000)])
+def test_smooth_lines_against_bluestein_and_oracle(ffst, shape, monkeypatch):
+    # 100, 150, 63, 250, 98, 343, 36 and 1000 have no prime factor above 7:
+    # mixed-radix lines by default, Bluestein lines with FFST_BLUESTEIN=1;
+    # both against the oracle, and not bitwise equal (two different engines)
+    f = _img(shape, 5)
+    x = torch.from_numpy(f).cuda()
+    p = ffst.Plan(*shape)
+    monkeypatch.setenv("FFST_BLUESTEIN", "1")
+    q = ffst.Plan(*shape)
+    monkeypatch.delenv("FFST_BLUESTEIN")
+    ref = o.forward(f.astype(np.float64))
+    cp, cq = p.forward(x), q.forward(x)
+    assert rel_l2(cp.cpu().numpy(), ref) <= FP32_TOL
+    assert rel_l2(cq.cpu().numpy(), ref) <= FP32_TOL
+    assert not torch.equal(cp, cq)
+    eta = p.num_planes
+    cnp = np.random.default_rng(shape[0] + shape[1]).standard_normal((eta,) + shape).astype(np.float32)
+    c = torch.from_numpy(cnp).cuda()
+    assert rel_l2(p.inverse(c).cpu().numpy(), o.inverse(cnp.astype(np.float64))) <= FP32_TOL
+    assert rel_l2(p.adjoint(c).cpu().numpy(), o.adjoint(cnp.astype(np.float64))) <= FP32_TOL
+    c16, s16 = p.forward(x, dtype=torch.float16)
+    assert rel_l2((c16.float() / s16.view(-1, 1, 1)).cpu().numpy(), ref) <= 2e-3
+    p.close()
+    q.close()
+
+
+@pytest.mark.parametrize("shape,planes", [((1080, 1920), [0, 9, 40, 77, 124]), ((700, 1000), [0, 5, 33, 60])])
+def test_large_smooth_sampled_planes(ffst, shape, planes):
+    # 1080 = 2^3 3^3 5 and 1920 = 2^7 3 5 (columns of 1080 points, rows of
+    # 1920 points as generic lines), 700 = 2^2 5^2 7 and 1000 = 2^3 5^3:
+    # sampled planes against the oracle, each relative to the plane's energy
+    # floored at 1e-3 of the image's, and the reconstruction
+    f = _img(shape, 12)
+    x = torch.from_numpy(f).cuda()
+    p = ffst.Plan(*shape)
+    c = p.forward(x)
+    F = np.fft.fft2(f.astype(np.float64))
+    for i in planes:
+        ref = o.forward_plane(F, p.scales, i)
+        got = c[i].cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-3 * np.linalg.norm(f))
+        assert err <= FP32_TOL, (i, err)
+    assert float(torch.linalg.norm(p.inverse(c) - x) / torch.linalg.norm(x)) <= FP32_TOL
+    del c
+    p.close()
