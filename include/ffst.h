@@ -34,13 +34,13 @@
  *    scales in 1..8 (or <= 0 for the default j0 of Sec. 3.1).  Columns of a
  *    height that is a power of two or one of 240, 320, 384, 480, 640, 768,
  *    and rows of a width that is twice one of those, run native FFT lines;
- *    any other height or width (at most 2048) runs generic lines and never
- *    the fused or persistent launches: a length with no prime factor above 7
- *    as mixed-radix passes in shared memory, any other length as Bluestein
- *    lines (a DFT of length n as a chirp convolution through power-of-two
- *    FFTs, several times slower per line; the environment variable
- *    FFST_BLUESTEIN=1 at plan creation selects them for every generic
- *    length).  Other sizes return FFST_ERR_UNSUPPORTED_SIZE.
+ *    any other height or width runs generic lines and never the fused or
+ *    persistent launches: a length with no prime factor above 7 (up to 4096)
+ *    as mixed-radix passes in shared memory, any other length (up to 2048)
+ *    as Bluestein lines (a DFT of length n as a chirp convolution through
+ *    power-of-two FFTs, several times slower per line; the environment
+ *    variable FFST_BLUESTEIN=1 at plan creation selects them for every
+ *    generic length).  Other sizes return FFST_ERR_UNSUPPORTED_SIZE.
  *    ffst_forward_noalloc keeps its own limits (powers of two).
  */
 #ifndef FFST_H

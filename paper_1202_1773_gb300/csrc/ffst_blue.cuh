@@ -53,8 +53,11 @@ void blue_tables(int n, int* L2, std::vector<float2>* chirp, std::vector<float2>
 // passes (8s, then a 4 or 2, then 3s, 5s, 7s) packed 4 bits per pass, and
 // the pass twiddle table (n - 1 entries).  False for other lengths.
 bool smooth_line(int n, int* nrad, unsigned long long* radices, std::vector<float2>* tw);
-// The power of two >= 2n - 1 (line geometry of the generic kernels).
+// Line geometry of the generic kernels: the power of two >= 2n - 1 for
+// Bluestein lines (their convolution length), >= n for smooth lines; at
+// least kBlueMinL2.
 int blue_L2(int n);
+int smooth_L2(int n);
 
 cudaError_t launch_blue_rows_r2c(const BlueLine& b, const R2CArgs& a, int nplanes, cudaStream_t s);
 cudaError_t launch_blue_rows_c2r(const BlueLine& b, const C2RArgs& a, int nplanes, cudaStream_t s);
@@ -101,7 +104,7 @@ __device__ __forceinline__ void smooth_pass(const float2* a, float2* c, int n, i
     float2 x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) x[r] = a[j + r * nb];
-    const int kk = j % Ns;
+    const int g = j / Ns, kk = j - g * Ns;
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -111,16 +114,16 @@ __device__ __forceinline__ void smooth_pass(const float2* a, float2* c, int n, i
       }
     }
     dft<R, INV>(x);
-    float2* dst = c + (j - kk) * R + kk;
+    float2* dst = c + g * Ns * R + kk;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[r * Ns] = x[r];
   }
 }
 
-// DFT (INV: unnormalised inverse) of length b.n, b.nrad > 0, of the line in
-// a[0, n) of a team's buffer, ping-ponging with c[0, n); returns the buffer
-// that holds the result.  Every thread of the block calls it: a barrier
-// follows each pass.  Not inlined: one copy serves every line geometry.
+// DFT (INV: unnormalised inverse) of length n, given as nrad > 0 radices,
+// of the line in a[0, n), ping-ponging with c[0, n); returns the buffer that
+// holds the result.  Every thread of the block calls it: a barrier follows
+// each pass.  Not inlined: one copy serves every line geometry.
 template <bool INV>
 __device__ __noinline__ float2* smooth_dft(float2* a, float2* c, int n, int nrad, unsigned long long radices,
                                            const float2* __restrict__ tw, int t, int T) {
@@ -144,26 +147,38 @@ __device__ __noinline__ float2* smooth_dft(float2* a, float2* c, int n, int nrad
   return a;
 }
 
+// Team buffer stride (float2 slots) and dynamic shared memory of a generic
+// line kernel: smooth lines ping-pong between two halves of BUF >= L2 >= n
+// slots each, Bluestein lines use one.
+template <int L2>
+__host__ __device__ __forceinline__ int blue_stride(const BlueLine& b) {
+  return b.nrad > 0 ? 2 * BlueCfg<L2>::BUF : BlueCfg<L2>::BUF;
+}
+template <int L2>
+__host__ __device__ __forceinline__ size_t blue_smem(const BlueLine& b) {
+  return sizeof(float2) * BlueCfg<L2>::P * (size_t)blue_stride<L2>(b);
+}
+
 // DFT (INV: unnormalised inverse DFT) of length b.n of the line whose
 // element j = t + T m (j < b.n; the rest is ignored) thread t holds in v[m];
 // on return v[m] holds output k = t + T m (zero for k >= b.n).  Every thread
 // of the block calls it (block barriers); it ends with a barrier after its
 // last read of `buf`.  Lengths with no prime factor above 7 run the
-// mixed-radix passes (buf holds 2n slots: L2 >= 2n); the others Bluestein's
-// convolution.
+// mixed-radix passes (lines laid out with L2 >= n, a team buffer of two
+// halves: blue_stride); the others Bluestein's convolution (L2 >= 2n - 1).
 template <int L2, bool INV>
 __device__ __forceinline__ void blue_dft(float2 (&v)[BlueCfg<L2>::E], float2* buf, int t, const BlueLine& b) {
   constexpr int E = BlueCfg<L2>::E, T = BlueCfg<L2>::T;
-  static_assert(BlueCfg<L2>::BUF >= L2, "a smooth line ping-pongs through 2n <= L2 buffer slots");
+  static_assert(BlueCfg<L2>::BUF >= L2, "each half of a smooth line's team buffer holds n <= L2 points");
   if (b.nrad > 0) {
-    __syncthreads();  // earlier reads of buf by other teams' threads are done
+    __syncthreads();  // earlier reads of buf by other threads of the team are done
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int j = t + T * m;
       if (j < b.n) buf[j] = v[m];
     }
     __syncthreads();
-    const float2* res = smooth_dft<INV>(buf, buf + b.n, b.n, b.nrad, b.radices, b.mtw, t, T);
+    const float2* res = smooth_dft<INV>(buf, buf + BlueCfg<L2>::BUF, b.n, b.nrad, b.radices, b.mtw, t, T);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int k = t + T * m;

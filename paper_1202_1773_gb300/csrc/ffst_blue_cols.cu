@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
     v[m] = x;
   }
-  blue_dft<L2, INV>(v, smem + cl * BlueCfg<L2>::BUF, t, b);
+  blue_dft<L2, INV>(v, smem + cl * blue_stride<L2>(b), t, b);
   if (act) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_blue_fwd_cols(FwdColsArgs a, Bl
   extern __shared__ __align__(128) float2 smem[];
   __shared__ float red[kThreads / 32];
   const int t = threadIdx.x / P, cl = threadIdx.x % P;
-  float2* buf = smem + cl * BlueCfg<L2>::BUF;
+  float2* buf = smem + cl * blue_stride<L2>(b);
   const int item = blockIdx.x;
   const int n = b.n;
   const ColItem it = a.items[item];
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_blue_inv_cols(InvColsArgs a, Bl
   constexpr int E = BlueCfg<L2>::E, T = BlueCfg<L2>::T, P = BlueCfg<L2>::P;
   extern __shared__ __align__(128) float2 smem[];
   const int t = threadIdx.x / P, cl = threadIdx.x % P;
-  float2* buf = smem + cl * BlueCfg<L2>::BUF;
+  float2* buf = smem + cl * blue_stride<L2>(b);
   const int n = b.n;
   int q0, q1;
   float2* S;
@@ -165,11 +165,11 @@ static cudaError_t cols_L2(const BlueLine& b, float2* buf, int width, int ld, bo
   if (grid <= 0) return cudaSuccess;
   cudaError_t e;
   if (inverse) {
-    if ((e = set_smem(k_blue_cols<L2, true>, BlueCfg<L2>::SMEM)) != cudaSuccess) return e;
-    k_blue_cols<L2, true><<<grid, kThreads, BlueCfg<L2>::SMEM, s>>>(buf, width, ld, scale_tab, nsum, sstride, b);
+    if ((e = set_smem(k_blue_cols<L2, true>, blue_smem<L2>(b))) != cudaSuccess) return e;
+    k_blue_cols<L2, true><<<grid, kThreads, blue_smem<L2>(b), s>>>(buf, width, ld, scale_tab, nsum, sstride, b);
   } else {
-    if ((e = set_smem(k_blue_cols<L2, false>, BlueCfg<L2>::SMEM)) != cudaSuccess) return e;
-    k_blue_cols<L2, false><<<grid, kThreads, BlueCfg<L2>::SMEM, s>>>(buf, width, ld, scale_tab, nsum, sstride, b);
+    if ((e = set_smem(k_blue_cols<L2, false>, blue_smem<L2>(b))) != cudaSuccess) return e;
+    k_blue_cols<L2, false><<<grid, kThreads, blue_smem<L2>(b), s>>>(buf, width, ld, scale_tab, nsum, sstride, b);
   }
   return cudaGetLastError();
 }
@@ -177,9 +177,9 @@ static cudaError_t cols_L2(const BlueLine& b, float2* buf, int width, int ld, bo
 template <int L2>
 static cudaError_t fwd_cols_L2(const BlueLine& b, const FwdColsArgs& a, int nitems, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
-  cudaError_t e = set_smem(k_blue_fwd_cols<L2>, BlueCfg<L2>::SMEM);
+  cudaError_t e = set_smem(k_blue_fwd_cols<L2>, blue_smem<L2>(b));
   if (e != cudaSuccess) return e;
-  k_blue_fwd_cols<L2><<<nitems, kThreads, BlueCfg<L2>::SMEM, s>>>(a, b);
+  k_blue_fwd_cols<L2><<<nitems, kThreads, blue_smem<L2>(b), s>>>(a, b);
   return cudaGetLastError();
 }
 
@@ -187,9 +187,9 @@ template <int L2>
 static cudaError_t inv_cols_L2(const BlueLine& b, const InvColsArgs& a, cudaStream_t s) {
   const int nb = a.npanels * a.nchunks;
   if (nb <= 0) return cudaSuccess;
-  cudaError_t e = set_smem(k_blue_inv_cols<L2>, BlueCfg<L2>::SMEM);
+  cudaError_t e = set_smem(k_blue_inv_cols<L2>, blue_smem<L2>(b));
   if (e != cudaSuccess) return e;
-  k_blue_inv_cols<L2><<<nb, kThreads, BlueCfg<L2>::SMEM, s>>>(a, b);
+  k_blue_inv_cols<L2><<<nb, kThreads, blue_smem<L2>(b), s>>>(a, b);
   return cudaGetLastError();
 }
 

@@ -16,6 +16,12 @@ int blue_L2(int n) {
   return L2;
 }
 
+int smooth_L2(int n) {
+  int L2 = kBlueMinL2;
+  while (L2 < n) L2 *= 2;
+  return L2;
+}
+
 bool smooth_line(int n, int* nrad, unsigned long long* radices, std::vector<float2>* tw) {
   std::vector<int> rs;
   int m = n;
@@ -126,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_blue_rows_r2c(R2CArgs a, BlueLi
   constexpr int E = BlueCfg<L2>::E, T = BlueCfg<L2>::T, P = BlueCfg<L2>::P;
   extern __shared__ __align__(128) float2 smem[];
   const int team = threadIdx.x / T, t = threadIdx.x % T;
-  float2* buf = smem + team * BlueCfg<L2>::BUF;
+  float2* buf = smem + team * blue_stride<L2>(b);
   const int n = b.n;
   const int by = blockIdx.y, plane = a.plane0 + by;
   const int r0 = 2 * (blockIdx.x * P + team), r1 = r0 + 1;
@@ -186,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_blue_rows_c2r(C2RArgs a, BlueLi
   extern __shared__ __align__(128) float2 smem[];
   __shared__ float red[kThreads / 32];
   const int team = threadIdx.x / T, t = threadIdx.x % T;
-  float2* buf = smem + team * BlueCfg<L2>::BUF;
+  float2* buf = smem + team * blue_stride<L2>(b);
   const int n = b.n;
   const int by = blockIdx.y, plane = a.plane0 + by;
   const int r0 = 2 * (blockIdx.x * P + team), r1 = r0 + 1;
@@ -272,9 +278,9 @@ static cudaError_t rows_r2c_L2(const BlueLine& b, const R2CArgs& a, int nplanes,
   constexpr int P = BlueCfg<L2>::P;
   const dim3 grid((unsigned)(((a.M + 1) / 2 + P - 1) / P), (unsigned)nplanes);
   if (nplanes <= 0 || a.M <= 0) return cudaSuccess;
-  cudaError_t e = set_smem(k_blue_rows_r2c<L2>, BlueCfg<L2>::SMEM);
+  cudaError_t e = set_smem(k_blue_rows_r2c<L2>, blue_smem<L2>(b));
   if (e != cudaSuccess) return e;
-  k_blue_rows_r2c<L2><<<grid, kThreads, BlueCfg<L2>::SMEM, s>>>(a, b);
+  k_blue_rows_r2c<L2><<<grid, kThreads, blue_smem<L2>(b), s>>>(a, b);
   return cudaGetLastError();
 }
 
@@ -283,9 +289,9 @@ static cudaError_t rows_c2r_L2(const BlueLine& b, const C2RArgs& a, int nplanes,
   constexpr int P = BlueCfg<L2>::P;
   const dim3 grid((unsigned)(((a.M + 1) / 2 + P - 1) / P), (unsigned)nplanes);
   if (nplanes <= 0 || a.M <= 0) return cudaSuccess;
-  cudaError_t e = set_smem(k_blue_rows_c2r<L2>, BlueCfg<L2>::SMEM);
+  cudaError_t e = set_smem(k_blue_rows_c2r<L2>, blue_smem<L2>(b));
   if (e != cudaSuccess) return e;
-  k_blue_rows_c2r<L2><<<grid, kThreads, BlueCfg<L2>::SMEM, s>>>(a, b);
+  k_blue_rows_c2r<L2><<<grid, kThreads, blue_smem<L2>(b), s>>>(a, b);
   return cudaGetLastError();
 }
 

@@ -571,15 +571,25 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
   if (vfun == FFST_V_POLY) vs = v_poly_spec(vorder);
   vs.kind = vfun;
   // native FFT lines: columns of length rows, rows as half-length complex
-  // lines of cols/2; any other length runs generic (Bluestein) lines of at
-  // most 2048 points
+  // lines of cols/2; any other length runs generic lines: mixed-radix for
+  // lengths with no prime factor above 7 (up to 4096 points), Bluestein for
+  // the others (up to 2048; FFST_BLUESTEIN=1: for every generic length)
+  const char* fb = std::getenv("FFST_BLUESTEIN");
+  const bool all_blue = fb && fb[0] == '1';
+  auto smooth7 = [](int n) {
+    for (int q : {2, 3, 5, 7})
+      while (n % q == 0) n /= q;
+    return n == 1;
+  };
+  auto generic_ok = [&](int n) { return n <= kBlueMaxL2 / 2 || (!all_blue && smooth7(n)); };
   const bool nat_cols = rows >= 8 && rows <= 4096 && supported_line(rows);
   const bool nat_rows = cols >= 8 && cols <= 4096 && cols % 2 == 0 && supported_line(cols / 2);
-  if (rows < 8 || cols < 8 || rows > 4096 || cols > 4096 || (!nat_cols && rows > kBlueMaxL2 / 2) ||
-      (!nat_rows && cols > kBlueMaxL2 / 2))
+  if (rows < 8 || cols < 8 || rows > 4096 || cols > 4096 || (!nat_cols && !generic_ok(rows)) ||
+      (!nat_rows && !generic_ok(cols)))
     return fail(FFST_ERR_UNSUPPORTED_SIZE,
-                "ffst_plan: rows and cols must be in [8, 4096], and at most 2048 unless rows is a power of two or "
-                "one of 240, 320, 384, 480, 640, 768 (cols: twice one of those), got " +
+                "ffst_plan: rows and cols must be in [8, 4096], and at most 2048 unless they have no prime factor "
+                "above 7, rows is a power of two or one of 240, 320, 384, 480, 640, 768 (cols: twice one of "
+                "those), got " +
                     std::to_string(rows) + "x" + std::to_string(cols));
   const int mx = rows > cols ? rows : cols;
   int lg = 0;
@@ -704,14 +714,11 @@ extern "C" ffst_status ffst_plan_ex(int rows, int cols, int scales, int variant,
     int L2s[2] = {0, 0};
     int nrads[2] = {0, 0};
     unsigned long long rcodes[2] = {0, 0};
-    // FFST_BLUESTEIN=1 keeps Bluestein lines for every generic length (A/B timing, tests)
-    const char* fb = std::getenv("FFST_BLUESTEIN");
-    const bool all_blue = fb && fb[0] == '1';
     for (int q = 0; q < 2; ++q) {
       if (!lens[q]) continue;
       std::vector<float2> mtw;
       if (!all_blue && smooth_line(lens[q], &nrads[q], &rcodes[q], &mtw)) {
-        L2s[q] = blue_L2(lens[q]);
+        L2s[q] = smooth_L2(lens[q]);
         off[q][0] = tab.size();
         tab.insert(tab.end(), mtw.begin(), mtw.end());
         continue;

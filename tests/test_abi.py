@@ -44,7 +44,7 @@ def test_status_strings(lib):
     assert _lib.status_name(99) == "FFST_ERR_UNKNOWN"
 
 
-@pytest.mark.parametrize("rows,cols,scales", [(0, 64, 0), (64, 0, 0), (3000, 64, 0), (64, 2050, 0), (2049, 63, 0),
+@pytest.mark.parametrize("rows,cols,scales", [(0, 64, 0), (64, 0, 0), (3001, 64, 0), (64, 2050, 0), (2049, 63, 0),
                                               (4, 64, 0), (64, 8192, 0), (64, 64, 9)])
 def test_unsupported_sizes_rejected_on_host(lib, rows, cols, scales):
     out = ctypes.c_void_p()
@@ -54,16 +54,27 @@ def test_unsupported_sizes_rejected_on_host(lib, rows, cols, scales):
     assert "ffst_plan" in _lib.last_error()
 
 
-@pytest.mark.parametrize("rows,cols", [(63, 64), (64, 63), (131, 137), (2048, 2047), (4096, 64), (2000, 4096)])
+@pytest.mark.parametrize("rows,cols", [(63, 64), (64, 63), (131, 137), (2048, 2047), (4096, 64), (2000, 4096),
+                                       (3000, 64), (2160, 3840), (64, 3087)])
 def test_generic_sizes_pass_the_size_check(lib, rows, cols):
     # odd, prime and other lengths without a native FFT line (Bluestein lines
-    # up to 2048; native lines up to 4096) are accepted: without a GPU the
+    # up to 2048, mixed-radix lines for lengths with no prime factor above 7
+    # up to 4096, native lines up to 4096) are accepted: without a GPU the
     # call fails later, in CUDA, never with FFST_ERR_UNSUPPORTED_SIZE
     out = ctypes.c_void_p()
     st = lib.ffst_plan(rows, cols, 0, ctypes.byref(out))
     if st == _lib.FFST_OK:
         lib.ffst_destroy(out)
     assert st != _lib.FFST_ERR_UNSUPPORTED_SIZE, _lib.last_error()
+
+
+def test_bluestein_switch_limits_generic_lengths(lib, monkeypatch):
+    # with FFST_BLUESTEIN=1 every generic length runs Bluestein lines, which
+    # stop at 2048: 3000 = 2^3 3 5^3 is then rejected on the host
+    monkeypatch.setenv("FFST_BLUESTEIN", "1")
+    out = ctypes.c_void_p()
+    assert lib.ffst_plan(3000, 64, 0, ctypes.byref(out)) == _lib.FFST_ERR_UNSUPPORTED_SIZE
+    assert out.value is None
 
 
 def test_null_arguments_rejected_on_host(lib):
@@ -97,7 +108,7 @@ def test_batch_and_graph_argument_errors_on_host(lib):
     assert lib.ffst_plan_batched(0, rows, cols, None, 4, ctypes.byref(out)) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_plan_batched(1, rows, cols, None, 0, ctypes.byref(out)) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_plan_batched(1, None, cols, None, 4, ctypes.byref(out)) == _lib.FFST_ERR_INVALID_ARG
-    bad = (ctypes.c_int * 1)(3000)
+    bad = (ctypes.c_int * 1)(3001)
     assert lib.ffst_plan_batched(1, bad, cols, None, 4, ctypes.byref(out)) == _lib.FFST_ERR_UNSUPPORTED_SIZE
     assert lib.ffst_batch_info(None, 0, None, None, None, None, None) == _lib.FFST_ERR_INVALID_ARG
     assert lib.ffst_forward_batched(None, None, None, 0, None, None) == _lib.FFST_ERR_INVALID_ARG

@@ -274,10 +274,12 @@ def test_smooth_lines_against_bluestein_and_oracle(ffst, shape, monkeypatch):
     q.close()
 
 
-@pytest.mark.parametrize("shape,planes", [((1080, 1920), [0, 9, 40, 77, 124]), ((700, 1000), [0, 5, 33, 60])])
+@pytest.mark.parametrize("shape,planes", [((1080, 1920), [0, 9, 40, 77, 124]), ((700, 1000), [0, 5, 33, 60]),
+                                          ((2160, 3840), [0, 61, 124])])
 def test_large_smooth_sampled_planes(ffst, shape, planes):
     # 1080 = 2^3 3^3 5 and 1920 = 2^7 3 5 (columns of 1080 points, rows of
-    # 1920 points as generic lines), 700 = 2^2 5^2 7 and 1000 = 2^3 5^3:
+    # 1920 points as generic lines), 700 = 2^2 5^2 7 and 1000 = 2^3 5^3,
+    # 2160 = 2^4 3^3 5 and 3840 = 2^8 3 5 (smooth lines above 2048 points):
     # sampled planes against the oracle, each relative to the plane's energy
     # floored at 1e-3 of the image's, and the reconstruction
     f = _img(shape, 12)
