@@ -120,6 +120,34 @@ int blue_lines_per_block(int L2) {
   }
 }
 
+// Elements j = t + T m (j < n) of rows r0 and r1 (when present) of a stack
+// of storage type ST, times f, as the line z = x_a + i x_b.
+template <int E, int T, int ST>
+__device__ __forceinline__ void load_row_pair(float2 (&v)[E], const void* src, int r0, int r1, bool a0, bool a1,
+                                              int n, int t, float f) {
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int j = t + T * m;
+    const float x0 = (a0 && j < n) ? load_one(src, (long long)r0 * n + j, ST) * f : 0.0f;
+    const float x1 = (a1 && j < n) ? load_one(src, (long long)r1 * n + j, ST) * f : 0.0f;
+    v[m] = make_float2(x0, x1);
+  }
+}
+
+// The line x_a + i x_b back to rows r0 and r1 (when present), elements
+// j = t + T m < n, in storage type ST.
+template <int E, int T, int ST>
+__device__ __forceinline__ void store_row_pair(const float2 (&v)[E], void* dst, int r0, int r1, bool a0, bool a1,
+                                               int n, int t) {
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int j = t + T * m;
+    if (j >= n) continue;
+    if (a0) store_one(dst, (long long)r0 * n + j, v[m].x, ST);
+    if (a1) store_one(dst, (long long)r1 * n + j, v[m].y, ST);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // row R2C: rows r0 = 2 (bx P + team) and r0 + 1 of plane plane0 + by as one
 // complex line z = x_a + i x_b; Z = DFT_n(z) goes through the team buffer and
@@ -147,13 +175,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_blue_rows_r2c(R2CArgs a, BlueLi
     f = 1.0f / __ldg(&a.plane_scale[plane]);
   }
   float2 v[E];
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int j = t + T * m;
-    const float x0 = (a0 && j < n) ? load_one(src, (long long)r0 * n + j, st) * f : 0.0f;
-    const float x1 = (a1 && j < n) ? load_one(src, (long long)r1 * n + j, st) * f : 0.0f;
-    v[m] = make_float2(x0, x1);
-  }
+  // one loop per storage type, so that all 2E loads of a thread are in
+  // flight together (a type switch per element serialises them)
+  if (st == FFST_STORE_F32) load_row_pair<E, T, FFST_STORE_F32>(v, src, r0, r1, a0, a1, n, t, f);
+  else if (st == FFST_STORE_F16) load_row_pair<E, T, FFST_STORE_F16>(v, src, r0, r1, a0, a1, n, t, f);
+  else load_row_pair<E, T, FFST_STORE_BF16>(v, src, r0, r1, a0, a1, n, t, f);
   blue_dft<L2, false>(v, buf, t, b);
 #pragma unroll
   for (int m = 0; m < E; ++m) {
@@ -264,13 +290,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_blue_rows_c2r(C2RArgs a, BlueLi
     }
   }
   void* dst = static_cast<char*>(a.dst) + (long long)by * a.dst_plane_stride * stor_bytes(a.st);
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int j = t + T * m;
-    if (j >= n) continue;
-    if (a0) store_one(dst, (long long)r0 * n + j, v[m].x, a.st);
-    if (a1) store_one(dst, (long long)r1 * n + j, v[m].y, a.st);
-  }
+  if (a.st == FFST_STORE_F32) store_row_pair<E, T, FFST_STORE_F32>(v, dst, r0, r1, a0, a1, n, t);
+  else if (a.st == FFST_STORE_F16) store_row_pair<E, T, FFST_STORE_F16>(v, dst, r0, r1, a0, a1, n, t);
+  else store_row_pair<E, T, FFST_STORE_BF16>(v, dst, r0, r1, a0, a1, n, t);
 }
 
 template <int L2>

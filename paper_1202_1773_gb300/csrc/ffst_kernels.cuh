@@ -183,15 +183,14 @@ __device__ __forceinline__ void rows_r2c_body(const R2CArgs& a, int bx, int by, 
   } else if (a.st == FFST_STORE_F32) {
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = load_pair_ck(src, rbase + 2 * T * m, FFST_STORE_F32, a.src, a.src_bytes, a.err);
-  } else {
-    const int st = a.st;
+  } else if (a.st == FFST_STORE_F16) {  // one loop per type: the loads of a thread fly together
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const float2 x = st == FFST_STORE_F16
-                           ? load_pair_ck(src, rbase + 2 * T * m, FFST_STORE_F16, a.src, a.src_bytes, a.err)
-                           : load_pair_ck(src, rbase + 2 * T * m, FFST_STORE_BF16, a.src, a.src_bytes, a.err);
-      v[m] = make_float2(x.x * us, x.y * us);
-    }
+    for (int m = 0; m < E; ++m)
+      v[m] = cscale(load_pair_ck(src, rbase + 2 * T * m, FFST_STORE_F16, a.src, a.src_bytes, a.err), us);
+  } else {
+#pragma unroll
+    for (int m = 0; m < E; ++m)
+      v[m] = cscale(load_pair_ck(src, rbase + 2 * T * m, FFST_STORE_BF16, a.src, a.src_bytes, a.err), us);
   }
   if constexpr (XSHFL) line_fft_shfl1024<false>(v, t, a.tw);
   else line_fft<L, E, false, C::SYNC>(v, buf, t, a.tw, 1 + team);
