@@ -96,6 +96,11 @@ __device__ __forceinline__ bool in_cyclic(int r, int2 rg, int n) {
 // takes a[j + r n/R], applies W_{Ns R}^{(j mod Ns) r} and the R-point DFT,
 // and writes c[(j - j mod Ns) R + j mod Ns + r Ns].  Team threads t, t + T,
 // ... share the butterflies.
+// Buffer slot of element i of a smooth line: one pad slot per 32 elements,
+// which spreads the radix-strided writes of the first passes over the banks
+// (a half of the team buffer holds n + n/32 <= L2 + L2/E slots).
+__device__ __forceinline__ int smooth_slot(int i) { return i + (i >> 5); }
+
 template <int R, bool INV>
 __device__ __forceinline__ void smooth_pass(const float2* a, float2* c, int n, int Ns, const float2* __restrict__ tw,
                                             int t, int T) {
@@ -103,7 +108,7 @@ __device__ __forceinline__ void smooth_pass(const float2* a, float2* c, int n, i
   for (int j = t; j < nb; j += T) {
     float2 x[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = a[j + r * nb];
+    for (int r = 0; r < R; ++r) x[r] = a[smooth_slot(j + r * nb)];
     const int g = j / Ns, kk = j - g * Ns;
     if (Ns > 1) {
 #pragma unroll
@@ -114,9 +119,9 @@ __device__ __forceinline__ void smooth_pass(const float2* a, float2* c, int n, i
       }
     }
     dft<R, INV>(x);
-    float2* dst = c + g * Ns * R + kk;
+    const int base = g * Ns * R + kk;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[r * Ns] = x[r];
+    for (int r = 0; r < R; ++r) c[smooth_slot(base + r * Ns)] = x[r];
   }
 }
 
@@ -169,20 +174,20 @@ __host__ __device__ __forceinline__ size_t blue_smem(const BlueLine& b) {
 template <int L2, bool INV>
 __device__ __forceinline__ void blue_dft(float2 (&v)[BlueCfg<L2>::E], float2* buf, int t, const BlueLine& b) {
   constexpr int E = BlueCfg<L2>::E, T = BlueCfg<L2>::T;
-  static_assert(BlueCfg<L2>::BUF >= L2, "each half of a smooth line's team buffer holds n <= L2 points");
+  static_assert(BlueCfg<L2>::BUF >= L2 + L2 / 32, "each half of a smooth line's team buffer holds n + n/32 slots");
   if (b.nrad > 0) {
     __syncthreads();  // earlier reads of buf by other threads of the team are done
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int j = t + T * m;
-      if (j < b.n) buf[j] = v[m];
+      if (j < b.n) buf[smooth_slot(j)] = v[m];
     }
     __syncthreads();
     const float2* res = smooth_dft<INV>(buf, buf + BlueCfg<L2>::BUF, b.n, b.nrad, b.radices, b.mtw, t, T);
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int k = t + T * m;
-      v[m] = k < b.n ? res[k] : make_float2(0.f, 0.f);
+      v[m] = k < b.n ? res[smooth_slot(k)] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     return;
