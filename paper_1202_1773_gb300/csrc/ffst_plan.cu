@@ -116,11 +116,32 @@ __global__ void k_support(WinParams w, const PlaneDesc* __restrict__ planes, int
   const int r0 = blockIdx.x * rows_per_block;
   const int r1 = min(w.M, r0 + rows_per_block);
   int lo = 0x7fffffff, hi = -1;
-  for (int e = threadIdx.x; e < (r1 - r0) * Hc; e += blockDim.x) {
-    const int pr = r0 + e / Hc, pc = e % Hc;
-    if (win_at(w, d, pr, pc) != 0.0f) {
-      lo = min(lo, pc);
-      hi = max(hi, pc);
+  // A classic h-cone plane is zero wherever its radial factor psi1(4^-j |xi1|)
+  // is (column pc, |omega1| = pc or N - pc), a v-cone plane wherever
+  // psi1(4^-j |xi2|) is (row pr); the Sec. 3.8.1 mirror keeps |omega|, so
+  // skipping those columns or rows finds the same extremes.
+  const bool radial = !w.smooth && (d.kappa == kH || d.kappa == kV);
+  if (radial && d.kappa == kH) {
+    for (int pc = threadIdx.x; pc < Hc; pc += blockDim.x) {
+      const int a1 = (2 * pc < w.N) ? pc : w.N - pc;
+      if (__ldg(&w.psi1_col[d.j * (w.hn + 1) + a1]) == 0.0f) continue;
+      for (int pr = r0; pr < r1; ++pr)
+        if (win_at(w, d, pr, pc) != 0.0f) {
+          lo = min(lo, pc);
+          hi = max(hi, pc);
+        }
+    }
+  } else {
+    for (int pr = r0; pr < r1; ++pr) {  // rows of the chunk, the threads across the columns
+      if (radial) {
+        const int a2 = (2 * pr < w.M) ? pr : w.M - pr;
+        if (__ldg(&w.psi1_row[d.j * (w.hm + 1) + a2]) == 0.0f) continue;  // uniform over the block
+      }
+      for (int pc = threadIdx.x; pc < Hc; pc += blockDim.x)
+        if (win_at(w, d, pr, pc) != 0.0f) {
+          lo = min(lo, pc);
+          hi = max(hi, pc);
+        }
     }
   }
   lo = __reduce_min_sync(0xffffffffu, lo);
